@@ -1,0 +1,269 @@
+"""CPU oracle of the avalanche-overlay hot path -- TEST INFRASTRUCTURE.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It wraps ``awo_oracle.c`` (plain C,
+compiled in FP32 and in FP64 with contraction off) through ctypes and shares no
+code with the CUDA library.
+
+Every function follows the paper's description of the avalanche workflow
+(Sec. 5.2) and overlay mipmap (Sec. 3); see the C source for the step-by-step
+reading.  ``precision`` selects the FP32 build (the parity oracle) or the FP64
+build (for closed-form pins).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+_LIBS: dict[str, ctypes.CDLL] = {}
+
+_U32P = ctypes.POINTER(ctypes.c_uint32)
+
+
+def _real(precision: str):
+    return (ctypes.c_float, np.float32) if precision == "f32" else (ctypes.c_double, np.float64)
+
+
+def _params_type(precision: str):
+    creal, _ = _real(precision)
+
+    class Params(ctypes.Structure):
+        _fields_ = [("mu", creal), ("drag_k", creal), ("persistence", creal),
+                    ("randomness", creal), ("step_scale", creal), ("gravity", creal),
+                    ("traj_per_cell", ctypes.c_uint32), ("max_steps", ctypes.c_uint32),
+                    ("seed", ctypes.c_uint64)]
+    return Params
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("total_steps", ctypes.c_uint64), ("n_traj", ctypes.c_uint64),
+                ("n_exited", ctypes.c_uint64), ("n_capped", ctypes.c_uint64),
+                ("n_stopped", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+_PARAMS = {p: _params_type(p) for p in ("f32", "f64")}
+
+
+def lib(precision: str = "f32") -> ctypes.CDLL:
+    if precision not in _LIBS:
+        path = _build.lib_path(precision)
+        if not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_build.SRC):
+            _build.build()
+        L = ctypes.CDLL(path)
+        L.orc_real_size.restype = ctypes.c_int
+        want = 4 if precision == "f32" else 8
+        if L.orc_real_size() != want:
+            raise RuntimeError(f"oracle {path} computes in {L.orc_real_size()}-byte reals, expected {want}")
+        _LIBS[precision] = L
+    return _LIBS[precision]
+
+
+def _ptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    assert a.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: status {code}")
+        self.code = code
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise OracleError(rc, what)
+
+
+# ----------------------------------------------------------------------------
+# Philox4x32-10
+# ----------------------------------------------------------------------------
+def philox4x32_10(ctr, key) -> tuple[int, int, int, int]:
+    c = (ctypes.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib("f32").orc_philox4x32_10(c, k, o)
+    return tuple(int(x) for x in o)
+
+
+def draw(cell: int, j: int, n: int, seed: int, precision: str = "f32") -> tuple[float, float]:
+    """The two uniforms in [-1, 1) that move n of trajectory (cell, j) uses."""
+    creal, npr = _real(precision)
+    xi = (creal * 2)()
+    lib(precision).orc_draw(ctypes.c_uint32(cell), ctypes.c_uint32(j), ctypes.c_uint32(n),
+                            ctypes.c_uint64(seed), xi)
+    return npr(xi[0]), npr(xi[1])
+
+
+def draws(cell: int, j: int, n_moves: int, seed: int, precision: str = "f32") -> np.ndarray:
+    return np.array([draw(cell, j, n, seed, precision) for n in range(n_moves)])
+
+
+# ----------------------------------------------------------------------------
+# Stages
+# ----------------------------------------------------------------------------
+def decode_u16(q: np.ndarray, scale: float = 0.1, precision: str = "f32") -> np.ndarray:
+    creal, npr = _real(precision)
+    q = np.ascontiguousarray(q, dtype=np.uint16)
+    h = np.empty(q.shape, dtype=npr)
+    lib(precision).orc_decode_u16(_ptr(q), ctypes.c_int64(q.size), creal(scale), _ptr(h))
+    return h
+
+
+def normals(h: np.ndarray, cs: float, precision: str = "f32", want_slope: bool = True):
+    """Returns (nrm[3,H,W], tan2[H,W], slope_deg[H,W] or None)."""
+    creal, npr = _real(precision)
+    h = np.ascontiguousarray(h, dtype=npr)
+    H, W = h.shape
+    nrm = np.empty((3, H, W), dtype=npr)
+    t2 = np.empty((H, W), dtype=npr)
+    sd = np.empty((H, W), dtype=npr) if want_slope else None
+    rc = lib(precision).orc_normals(_ptr(h), ctypes.c_int32(W), ctypes.c_int32(H), creal(cs),
+                                    _ptr(nrm), _ptr(t2), _ptr(sd))
+    _check(rc, "orc_normals")
+    return nrm, t2, sd
+
+
+def release(tan2: np.ndarray, lo_deg: float, hi_deg: float, precision: str = "f32"):
+    """Returns (mask[H,W] uint8, cells uint32 sorted)."""
+    _, npr = _real(precision)
+    t2 = np.ascontiguousarray(tan2, dtype=npr)
+    H, W = t2.shape
+    mask = np.empty((H, W), dtype=np.uint8)
+    cells = np.empty(W * H, dtype=np.uint32)
+    n = ctypes.c_uint32(0)
+    rc = lib(precision).orc_release(_ptr(t2), ctypes.c_int32(W), ctypes.c_int32(H),
+                                    ctypes.c_double(lo_deg), ctypes.c_double(hi_deg),
+                                    _ptr(mask), _ptr(cells), ctypes.byref(n))
+    _check(rc, "orc_release")
+    return mask, cells[: n.value].copy()
+
+
+@dataclass
+class SimParams:
+    mu: float = 0.46630765815499864  # tan(25 deg)
+    drag_k: float = 0.0
+    persistence: float = 0.9
+    randomness: float = 0.16
+    step_scale: float = 1.0
+    gravity: float = 9.81
+    traj_per_cell: int = 16
+    max_steps: int = 1000
+    seed: int = 0
+
+    def to_c(self, precision: str):
+        return _PARAMS[precision](self.mu, self.drag_k, self.persistence, self.randomness,
+                                  self.step_scale, self.gravity, self.traj_per_cell,
+                                  self.max_steps, self.seed)
+
+
+def simulate(h: np.ndarray, cs: float, cells: np.ndarray, params: SimParams,
+             precision: str = "f32", count64: np.ndarray | None = None,
+             maxe: np.ndarray | None = None):
+    """Accumulates into (count64 uint64[H,W], maxe real[H,W]); returns them and stats."""
+    creal, npr = _real(precision)
+    h = np.ascontiguousarray(h, dtype=npr)
+    H, W = h.shape
+    cells = np.ascontiguousarray(cells, dtype=np.uint32)
+    if count64 is None:
+        count64 = np.zeros((H, W), dtype=np.uint64)
+    if maxe is None:
+        maxe = np.zeros((H, W), dtype=npr)
+    st = Stats()
+    p = params.to_c(precision)
+    rc = lib(precision).orc_simulate(_ptr(h), ctypes.c_int32(W), ctypes.c_int32(H), creal(cs),
+                                     _ptr(cells), ctypes.c_uint32(cells.size), ctypes.byref(p),
+                                     _ptr(count64), _ptr(maxe), ctypes.byref(st))
+    _check(rc, "orc_simulate")
+    return count64, maxe, st.as_dict()
+
+
+def counts_u32(count64: np.ndarray) -> np.ndarray:
+    """Count raster as uint32; raises OracleError(5) where a cell exceeds 2^32-1."""
+    if count64.size and int(count64.max()) > 0xFFFFFFFF:
+        raise OracleError(5, "count overflow")
+    return count64.astype(np.uint32)
+
+
+END_NAMES = {0: "capped", 1: "exited", 2: "stopped"}
+
+
+def trace(h: np.ndarray, cs: float, cell: int, j: int, params: SimParams,
+          precision: str = "f32", cap: int | None = None) -> dict:
+    creal, npr = _real(precision)
+    h = np.ascontiguousarray(h, dtype=npr)
+    H, W = h.shape
+    cap = cap if cap is not None else params.max_steps + 1
+    u = np.empty(cap, dtype=npr)
+    v = np.empty(cap, dtype=npr)
+    e = np.empty(cap, dtype=npr)
+    c = np.empty(cap, dtype=np.int64)
+    n = ctypes.c_int64(0)
+    end = ctypes.c_int32(0)
+    p = params.to_c(precision)
+    rc = lib(precision).orc_trace(_ptr(h), ctypes.c_int32(W), ctypes.c_int32(H), creal(cs),
+                                  ctypes.c_uint32(cell), ctypes.c_uint32(j), ctypes.byref(p),
+                                  ctypes.c_int64(cap), _ptr(u), _ptr(v), _ptr(e), _ptr(c),
+                                  ctypes.byref(n), ctypes.byref(end))
+    _check(rc, "orc_trace")
+    k = n.value
+    return {"u": u[:k].copy(), "v": v[:k].copy(), "e": e[:k].copy(), "cell": c[:k].copy(),
+            "end": END_NAMES[end.value]}
+
+
+def finalize(maxe: np.ndarray, gravity: float = 9.81, precision: str = "f32") -> np.ndarray:
+    creal, npr = _real(precision)
+    m = np.ascontiguousarray(maxe, dtype=npr)
+    vel = np.empty_like(m)
+    lib(precision).orc_finalize(_ptr(m), ctypes.c_int64(m.size), creal(gravity), _ptr(vel))
+    return vel
+
+
+def lod(count: np.ndarray, vel: np.ndarray, levels: int, precision: str = "f32"):
+    """Returns lists of count and vel rasters for levels 0..levels-1 (level 0 = inputs)."""
+    _, npr = _real(precision)
+    count = np.ascontiguousarray(count, dtype=np.uint32)
+    vel = np.ascontiguousarray(vel, dtype=npr)
+    H, W = count.shape
+    cs_out, vs_out = [], []
+    w, hh = W, H
+    for _ in range(1, levels):
+        w, hh = (w + 1) // 2, (hh + 1) // 2
+        cs_out.append(np.empty((hh, w), dtype=np.uint32))
+        vs_out.append(np.empty((hh, w), dtype=npr))
+    n = max(levels - 1, 1)
+    cp = (ctypes.c_void_p * n)(*[a.ctypes.data for a in cs_out] or [None])
+    vp = (ctypes.c_void_p * n)(*[a.ctypes.data for a in vs_out] or [None])
+    rc = lib(precision).orc_lod(_ptr(count), _ptr(vel), ctypes.c_int32(W), ctypes.c_int32(H),
+                                ctypes.c_int32(levels), cp, vp)
+    _check(rc, "orc_lod")
+    return [count] + cs_out, [vel] + vs_out
+
+
+def tan2_threshold(deg: float, precision: str = "f32") -> float:
+    """tan^2 of an angle in degrees, computed in FP64 and rounded once."""
+    _, npr = _real(precision)
+    t = np.tan(np.float64(deg) * (np.pi / 180.0))
+    return npr(t * t)
+
+
+def overlay(h: np.ndarray, cs: float, lo_deg: float, hi_deg: float, params: SimParams,
+            levels: int = 1, precision: str = "f32") -> dict:
+    """The whole workflow: normals -> release -> simulate -> velocity -> mipmap."""
+    nrm, t2, sd = normals(h, cs, precision)
+    mask, cells = release(t2, lo_deg, hi_deg, precision)
+    c64, maxe, st = simulate(h, cs, cells, params, precision)
+    count = counts_u32(c64)
+    vel = finalize(maxe, params.gravity, precision)
+    cl, vl = lod(count, vel, levels, precision)
+    return {"normals": nrm, "tan2": t2, "slope_deg": sd, "mask": mask, "cells": cells,
+            "count": count, "maxe": maxe, "vel": vel, "count_lv": cl, "vel_lv": vl, "stats": st}

@@ -1,0 +1,210 @@
+"""Seeded synthetic terrain for the avalanche-overlay workloads.
+
+This module only makes inputs: digital elevation models (DEMs) with the shapes
+of the paper's workloads (Sec. 5.2: 5-10 m alpine DEMs, release cells by
+steepness range, many particles per release cell).  The paper's own datasets
+(*parabola*, *vals*) are not available, so these generators stand in for them.
+It contains none of the method's arithmetic (no normals, release test,
+trajectories or mipmaps); both the CUDA path and the CPU oracle receive the
+arrays made here.
+
+Recipes (all deterministic for a given seed):
+
+* ``tiny``: 256 x 256 FP32 heights, 10 m cells.  An inclined plane falling at
+  35 degrees towards +y, plus a Gaussian bump (+80 m, sigma 20 cells, centred
+  at column 128, row 80), plus a V-shaped gully along column 128 whose sides
+  rise at 10 degrees.
+* ``fbm``: fractal Brownian terrain by spectral synthesis -- complex Gaussian
+  noise shaped to a power spectrum proportional to |f|^-(2H+2) (Hurst
+  exponent H), inverse FFT, rescaled to [0, relief] metres.
+* ``carve_valleys``: lowers an fBm surface along a drainage network.  Flow
+  accumulation A is computed by steepest-descent (D8) routing on an 8x
+  block-averaged copy; the carve depth min(c sqrt(A), 150 m) is upsampled
+  bilinearly and subtracted; the result is rescaled to [0, relief].
+* Quantisation: heights in decimetres, ``round(h * 10)`` stored as uint16
+  (the decode back to FP32 is a step of the method and is not done here).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+CELL_SIZE_M = 10.0
+DECODE_SCALE = 0.1  # metres per stored uint16 unit (decimetres)
+
+
+# ----------------------------------------------------------------------------
+# Primitive surfaces
+# ----------------------------------------------------------------------------
+def plane(W: int, H: int, cs: float, tan_theta: float, azimuth_deg: float = 90.0,
+          z0: float = 2000.0, dtype=np.float32) -> np.ndarray:
+    """Plane falling with slope tan_theta towards azimuth (0 = +x, 90 = +y)."""
+    a = np.deg2rad(azimuth_deg)
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    z = z0 - tan_theta * cs * (x * np.cos(a) + y * np.sin(a))
+    return z.astype(dtype)
+
+
+def plane_to_flat(W: int, H: int, cs: float, tan_theta: float, slope_rows: int,
+                  z0: float = 2000.0, dtype=np.float32) -> np.ndarray:
+    """Falls towards +y at tan_theta for ``slope_rows`` rows, then flat."""
+    y = np.arange(H, dtype=np.float64)
+    prof = z0 - tan_theta * cs * np.minimum(y, slope_rows)
+    return np.broadcast_to(prof[:, None], (H, W)).astype(dtype).copy()
+
+
+def tiny_dem(W: int = 256, H: int = 256, cs: float = CELL_SIZE_M) -> np.ndarray:
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    z = 2000.0 - y * cs * np.tan(np.deg2rad(35.0))
+    z += 80.0 * np.exp(-((x - 128.0) ** 2 + (y - 80.0) ** 2) / (2.0 * 20.0 ** 2))
+    z += np.abs(x - 128.0) * cs * np.tan(np.deg2rad(10.0))
+    return z.astype(np.float32)
+
+
+def fbm(n: int, hurst: float, seed: int, relief: float = 3000.0, m: int | None = None) -> np.ndarray:
+    """n (rows) x m (cols) fBm heights in [0, relief] (float64)."""
+    m = n if m is None else m
+    rng = np.random.default_rng(seed)
+    ky = np.fft.fftfreq(n)[:, None]
+    kx = np.fft.rfftfreq(m)[None, :]
+    f = np.sqrt(kx * kx + ky * ky)
+    f[0, 0] = np.inf
+    amp = f ** (-(hurst + 1.0))
+    spec = amp * (rng.standard_normal(f.shape) + 1j * rng.standard_normal(f.shape))
+    del f, amp
+    z = np.fft.irfft2(spec, s=(n, m))
+    del spec
+    z -= z.min()
+    z *= relief / z.max()
+    return z
+
+
+def _d8_accumulation(z: np.ndarray) -> np.ndarray:
+    """Number of cells draining through each cell under steepest descent."""
+    H, W = z.shape
+    pad = np.pad(z, 1, mode="edge")
+    best = np.zeros((H, W))
+    recv = -np.ones((H, W), dtype=np.int64)
+    idx = np.arange(H * W).reshape(H, W)
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            if dx == 0 and dy == 0:
+                continue
+            nb = pad[1 + dy:1 + dy + H, 1 + dx:1 + dx + W]
+            drop = (z - nb) / np.hypot(dx, dy)
+            ys = np.clip(np.arange(H) + dy, 0, H - 1)[:, None]
+            xs = np.clip(np.arange(W) + dx, 0, W - 1)[None, :]
+            take = drop > best
+            best = np.where(take, drop, best)
+            recv = np.where(take, idx[ys, xs], recv)
+    order = np.argsort(-z.ravel(), kind="stable").tolist()
+    r = recv.ravel().tolist()
+    acc = [1.0] * (H * W)
+    for i in order:
+        t = r[i]
+        if t >= 0:
+            acc[t] += acc[i]
+    return np.asarray(acc).reshape(H, W)
+
+
+def carve_valleys(z: np.ndarray, factor: int = 8, c: float = 2.0, cap: float = 150.0,
+                  relief: float = 3000.0) -> np.ndarray:
+    from scipy.ndimage import zoom
+    H, W = z.shape
+    coarse = z[: H - H % factor, : W - W % factor].reshape(H // factor, factor, W // factor, factor).mean(axis=(1, 3))
+    acc = _d8_accumulation(coarse)
+    depth = np.minimum(c * np.sqrt(acc), cap)
+    depth = zoom(depth, (H / depth.shape[0], W / depth.shape[1]), order=1)[:H, :W]
+    out = z - depth
+    out -= out.min()
+    out *= relief / out.max()
+    return out
+
+
+def quantise_dm(h: np.ndarray) -> np.ndarray:
+    """Heights in metres -> uint16 decimetres, round half to even."""
+    q = np.rint(np.asarray(h, dtype=np.float64) * 10.0)
+    if q.min() < 0 or q.max() > 65535:
+        raise ValueError("heights out of the uint16 decimetre range")
+    return q.astype(np.uint16)
+
+
+# ----------------------------------------------------------------------------
+# Workloads
+# ----------------------------------------------------------------------------
+@dataclass
+class Workload:
+    """A DEM plus the workflow parameters of one configuration."""
+    name: str
+    width: int
+    height: int
+    cell_size: float
+    slope_lo_deg: float
+    slope_hi_deg: float
+    traj_per_cell: int
+    max_steps: int
+    lod_levels: int
+    seed: int = 0
+    mu: float = float(np.tan(np.deg2rad(25.0)))
+    drag_k: float = 0.0
+    persistence: float = 0.9
+    randomness: float = 0.16
+    step_scale: float = 1.0
+    gravity: float = 9.81
+    dem_u16: np.ndarray | None = field(default=None, repr=False)
+    dem_f32: np.ndarray | None = field(default=None, repr=False)
+
+    @property
+    def quantised(self) -> bool:
+        return self.dem_u16 is not None
+
+    def describe(self) -> dict:
+        return {"workload": self.name, "dem": f"{self.width}x{self.height}",
+                "cell_m": self.cell_size, "dem_storage": "uint16 dm" if self.quantised else "fp32",
+                "release_deg": [self.slope_lo_deg, self.slope_hi_deg],
+                "traj_per_cell": self.traj_per_cell, "max_steps": self.max_steps,
+                "lod_levels": self.lod_levels, "persistence": self.persistence,
+                "randomness": self.randomness, "runout_deg": round(float(np.rad2deg(np.arctan(self.mu))), 6),
+                "drag_k": self.drag_k, "seed": self.seed}
+
+
+# Release ranges of the fBm workloads.  The recipe asks for about 5% release
+# cells; [30, 45] degrees selects 37% of the 2048^2 surface and 2.6% of the
+# 8192^2 one, so the lower bound is moved to the value found by
+# tests/golden/calibrate_release.py (0.1 degree grid, FP64 steepness).
+MID_RELEASE_DEG = (43.1, 45.0)    # 4.87% of the 2048^2 cells
+LARGE_RELEASE_DEG = (27.6, 45.0)  # 5.01% of the 8192^2 cells
+
+
+def tiny() -> Workload:
+    return Workload("tiny-256", 256, 256, CELL_SIZE_M, 30.0, 45.0, traj_per_cell=16,
+                    max_steps=1000, lod_levels=1, seed=0, dem_f32=tiny_dem())
+
+
+def mid(n: int = 2048) -> Workload:
+    z = fbm(n, 0.8, seed=1)
+    return Workload(f"mid-fbm-{n}", n, n, CELL_SIZE_M, *MID_RELEASE_DEG, traj_per_cell=64,
+                    max_steps=4000, lod_levels=1, seed=0, dem_u16=quantise_dm(z))
+
+
+def large_dem_u16(n: int = 8192) -> np.ndarray:
+    return quantise_dm(carve_valleys(fbm(n, 0.8, seed=2)))
+
+
+def large(n: int = 8192) -> Workload:
+    return Workload(f"large-fbm-valleys-{n}", n, n, CELL_SIZE_M, *LARGE_RELEASE_DEG,
+                    traj_per_cell=256, max_steps=8000, lod_levels=6, seed=0,
+                    dem_u16=large_dem_u16(n))
+
+
+def crop(w: Workload, n: int) -> Workload:
+    """Top-left n x n crop of a workload, as a DEM of its own."""
+    out = Workload(f"{w.name}-crop{n}", n, n, w.cell_size, w.slope_lo_deg, w.slope_hi_deg,
+                   w.traj_per_cell, w.max_steps, w.lod_levels, w.seed, w.mu, w.drag_k,
+                   w.persistence, w.randomness, w.step_scale, w.gravity)
+    if w.dem_u16 is not None:
+        out.dem_u16 = np.ascontiguousarray(w.dem_u16[:n, :n])
+    if w.dem_f32 is not None:
+        out.dem_f32 = np.ascontiguousarray(w.dem_f32[:n, :n])
+    return out
