@@ -1,0 +1,423 @@
+#!/usr/bin/env python3
+"""Benchmark of the avalanche-overlay hot path on GB300.
+
+One step = the whole workflow over the 8192 x 8192 synthetic DEM (fBm plus a
+carved valley network, 10 m cells, uint16 decimetres): decode -> normals ->
+release (about 5% of the cells) -> 256 particles per release cell (step cap
+8000) -> velocity -> 6-level mipmap, with the DEM already resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl awo|reference]
+
+Prints one JSON line (rank 0).  ``value`` is trajectory steps (recorded
+particle moves) per second over the whole step; ``ms_per_step`` is ms per
+overlay.  ``--impl reference`` times the CPU oracle on the host cores on
+bounded samples of the same workload.  Under torchrun every rank runs its own
+replica of the workload (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "trajectory-steps/s and ms/overlay at 8192^2 DEM on 1 GB300; % of gather roofline"
+UNIT = "trajectory-steps/s"
+
+# Bytes per visit of the particle kernel that the roofline counts as
+# algorithmic: a 2x2 FP32 height footprint (16 B) plus two 4-byte reductions
+# (count, energy) for a move, or one reduction plus the 4-byte release-index
+# read for a release visit.
+ALG_BYTES_PER_VISIT = 24
+
+# DRAM bytes per visit of the particle kernel from an ncu capture (dram__bytes
+# read + write), keyed by the SHA-256 of the kernel source it was taken on;
+# a changed kernel reports traffic null until it is captured again.
+DRAM_BYTES_PER_VISIT: dict[str, float] = {}
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["awo", "reference"], default="awo")
+    ap.add_argument("--workload", choices=["large", "mid", "tiny"], default="large")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# ranks
+# ----------------------------------------------------------------------------
+class Ranks:
+    def __init__(self):
+        import torch
+        import torch.distributed as dist
+
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = dist if self.world > 1 else None
+        self.torch = torch
+        if self.dist is not None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend)
+        self.device = torch.device("cuda", self.local) if torch.cuda.is_available() else torch.device("cpu")
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def reduce(self, x: float, op: str) -> float:
+        if self.dist is None:
+            return x
+        t = self.torch.tensor([float(x)], dtype=self.torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX if op == "max" else self.dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+_REASON_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
+                0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+                0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting"}
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = None
+        self.sel = []
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            if uuid:
+                self.sel = ["-i", uuid if uuid.startswith("GPU-") else "GPU-" + uuid]
+        except Exception:
+            self.sel = []
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="awo_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", *self.sel, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]) if parts[3] not in ("[N/A]", "N/A") else 0.0,
+                             int(parts[4], 16) if parts[4].startswith("0x") else 0, parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [r for r in rows if r[2] > 0 and not (r[3] & 0x1)] or rows
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in loaded:
+            for bit, name in _REASON_BITS.items():
+                if r[3] & bit and name != "gpu_idle":
+                    reasons.add(name)
+            for name, flag in zip(names, r[4]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(loaded), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# workload
+# ----------------------------------------------------------------------------
+def _workload(name: str):
+    from paper_2506_23364_gb300 import inputs
+    return {"large": inputs.large, "mid": inputs.mid, "tiny": inputs.tiny}[name]()
+
+
+def _peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _kernel_sha() -> str:
+    p = os.path.join(ROOT, "paper_2506_23364_gb300", "csrc", "awo_simulate.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def _probe_peaks(torch, awo) -> dict:
+    """L2 scattered-load and scattered-reduction rates, best of 5 (events)."""
+    buf = torch.zeros(8 << 20, dtype=torch.int32, device="cuda")  # 32 MiB: L2-resident
+    sink = torch.empty(awo.awo_probe_threads(), dtype=torch.int32, device="cuda")
+    iters = 256
+    out = {}
+    for name, fn, per in (("l2_gather", lambda: awo.awo_probe_l2_gather(buf, iters, sink), 4),
+                          ("l2_red", lambda: awo.awo_probe_l2_red(buf, iters), 2)):
+        fn()
+        torch.cuda.synchronize()
+        best = math.inf
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            best = min(best, a.elapsed_time(b) / 1e3)
+        out[name + "_per_s"] = awo.awo_probe_threads() * iters * per / best
+    return out
+
+
+def _cpu_baseline(w, seconds: float, threads: int | None = None) -> dict:
+    """The oracle, as it stands, on the host cores over a random sample of the
+    workload's release cells (all particles of each sampled cell)."""
+    import numpy as np
+
+    import oracle
+
+    h = oracle.decode_u16(w.dem_u16) if w.dem_u16 is not None else w.dem_f32
+    _, t2, _ = oracle.normals(h, w.cell_size, want_slope=False)
+    _, cells = oracle.release(t2, w.slope_lo_deg, w.slope_hi_deg)
+    p = oracle.SimParams(mu=w.mu, drag_k=w.drag_k, persistence=w.persistence, randomness=w.randomness,
+                         step_scale=w.step_scale, gravity=w.gravity, traj_per_cell=w.traj_per_cell,
+                         max_steps=w.max_steps, seed=w.seed)
+    threads = threads or os.cpu_count() or 1
+    rng = np.random.default_rng(12345)
+    probe = np.sort(rng.choice(cells, min(cells.size, 64 * threads), replace=False))
+    t0 = time.perf_counter()
+    oracle.simulate_threaded(h, w.cell_size, probe, p, threads=threads, merge=False)
+    rate = probe.size / max(time.perf_counter() - t0, 1e-6)
+    k = int(min(cells.size, max(threads, rate * seconds)))
+    sample = np.sort(rng.choice(cells, k, replace=False))
+    t0 = time.perf_counter()
+    _, _, st = oracle.simulate_threaded(h, w.cell_size, sample, p, threads=threads, merge=False)
+    dt = time.perf_counter() - t0
+    return {"value": st["total_steps"] / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": (f"{k} of {cells.size} release cells (uniform random, seed 12345), all "
+                       f"{w.traj_per_cell} particles each: {st['n_traj']} particles, {st['total_steps']} moves "
+                       f"in {dt:.2f} s on {threads} threads"),
+            "particles_per_s": st["n_traj"] / dt, "seconds": dt}
+
+
+# ----------------------------------------------------------------------------
+# arms
+# ----------------------------------------------------------------------------
+def run_awo(args, R: Ranks):
+    import numpy as np
+    import torch
+
+    import paper_2506_23364_gb300 as awo
+
+    w = _workload(args.workload)
+    params = awo.SimParams.make(mu=w.mu, drag_k=w.drag_k, persistence=w.persistence, randomness=w.randomness,
+                                step_scale=w.step_scale, gravity=w.gravity, traj_per_cell=w.traj_per_cell,
+                                max_steps=w.max_steps, seed=w.seed)
+    ov = awo.Overlay(w.width, w.height, w.cell_size, quantised=w.quantised, levels=w.lod_levels,
+                     device=R.device, want_slope=False)
+    host_dem = w.dem_u16 if w.quantised else w.dem_f32
+    ov.load_dem(host_dem)
+    torch.cuda.synchronize()
+    lo, hi = w.slope_lo_deg, w.slope_hi_deg
+
+    def step(ev=None):
+        ov.terrain(lo, hi)
+        if ev is not None:
+            ev[0].record()
+        ov.simulate(params)
+        if ev is not None:
+            ev[1].record()
+        ov.overlay(w.gravity)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    st = ov.stats_dict()
+    visits = st["total_steps"] + st["n_traj"]
+    launches_per_step = (1 if w.quantised else 0) + 1 + 3 + 1 + 1 + max(w.lod_levels - 1, 0)
+
+    peaks_probe = _probe_peaks(torch, awo)
+    clocks = ClockSampler(R.local)
+    sim_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    R.barrier()
+    torch.cuda.synchronize()
+    t0.record()
+    for k in range(args.steps):
+        step(sim_ev[k])
+    t1.record()
+    torch.cuda.synchronize()
+    R.barrier()
+    clk = clocks.stop()
+    ms_step = t0.elapsed_time(t1) / args.steps
+    sim_ms = statistics.mean(a.elapsed_time(b) for a, b in sim_ev)
+    st2 = ov.stats_dict()
+    assert st2 == st, "particle statistics changed between runs"
+    ms_step_max = R.reduce(ms_step, "max")
+    total_steps_all = R.reduce(float(st["total_steps"]), "sum")
+    value = total_steps_all / (ms_step_max / 1e3)
+
+    # end to end through the API with host buffers: H2D of the DEM, D2H of the overlay (all levels)
+    pin_dem = torch.from_numpy(np.ascontiguousarray(host_dem).view(np.int16) if w.quantised else host_dem).pin_memory()
+    outs = [(ov.count, torch.empty(ov.count.shape, dtype=torch.int32).pin_memory()),
+            (ov.vel, torch.empty(ov.vel.shape, dtype=torch.float32).pin_memory())]
+    for c, v in zip(ov.count_lv, ov.vel_lv):
+        outs.append((c, torch.empty(c.shape, dtype=torch.int32).pin_memory()))
+        outs.append((v, torch.empty(v.shape, dtype=torch.float32).pin_memory()))
+    bi = pin_dem.numel() * pin_dem.element_size()
+    bo = sum(h.numel() * h.element_size() for _, h in outs)
+    dst = ov.q if w.quantised else ov.h
+    e2e_ms = []
+    for k in range(max(args.e2e_steps, 1) + 1):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        R.barrier()
+        a.record()
+        dst.copy_(pin_dem, non_blocking=True)
+        step()
+        for d, h in outs:
+            h.copy_(d, non_blocking=True)
+        b.record()
+        b.synchronize()
+        if k > 0:
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_step = R.reduce(statistics.mean(e2e_ms), "max")
+    e2e_value = total_steps_all / (e2e_step / 1e3)
+
+    peaks = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    alg_bytes = ALG_BYTES_PER_VISIT * visits
+    achieved = alg_bytes / (sim_ms / 1e3) / 1e9
+    sha = _kernel_sha()
+    traffic = DRAM_BYTES_PER_VISIT.get(sha)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": traffic * visits if traffic is not None else None, "kernel": "k_simulate",
+                "kernel_ms": sim_ms, "alg_bytes_per_launch": alg_bytes,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
+    l2 = {"gather_loads_per_s": 4 * visits / (sim_ms / 1e3), "red_per_s": 2 * visits / (sim_ms / 1e3),
+          "probe_l2_gather_loads_per_s": peaks_probe["l2_gather_per_s"],
+          "probe_l2_red_per_s": peaks_probe["l2_red_per_s"]}
+    l2["gather_frac"] = l2["gather_loads_per_s"] / l2["probe_l2_gather_loads_per_s"]
+    l2["red_frac"] = l2["red_per_s"] / l2["probe_l2_red_per_s"]
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": R.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded fBm + carved valleys, uint16 dm)",
+            "config": dict(w.describe(), parallelism=f"replicas x{R.world}" if R.world > 1 else "single GPU",
+                           l2="inputs larger than L2 (uint16 DEM 128 MiB + FP32 DEM 256 MiB + rasters)",
+                           release_cells=ov.n_release()),
+            "ms_per_overlay": ms_step_max, "simulate_ms": sim_ms,
+            "simulate_steps_per_s": st["total_steps"] / (sim_ms / 1e3),
+            "particles_per_s": st["n_traj"] / (sim_ms / 1e3), "stats": st,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+                    "ms_per_step": e2e_step},
+            "gpu_launches": launches_per_step * args.steps, "roofline": roofline, "roofline_l2": l2,
+            "clocks": clk, "kernel_sha": sha}
+    if R.rank == 0 and R.world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline(w, args.cpu_seconds)
+    if R.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_reference(args, R: Ranks):
+    """The CPU oracle on the host cores: each step a bounded random sample of
+    the workload's release cells (all particles of each)."""
+    if R.rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+
+    w = _workload(args.workload)
+    h = oracle.decode_u16(w.dem_u16) if w.dem_u16 is not None else w.dem_f32
+    _, t2, _ = oracle.normals(h, w.cell_size, want_slope=False)
+    _, cells = oracle.release(t2, w.slope_lo_deg, w.slope_hi_deg)
+    p = oracle.SimParams(mu=w.mu, drag_k=w.drag_k, persistence=w.persistence, randomness=w.randomness,
+                         step_scale=w.step_scale, gravity=w.gravity, traj_per_cell=w.traj_per_cell,
+                         max_steps=w.max_steps, seed=w.seed)
+    threads = os.cpu_count() or 1
+    total = args.steps + max(args.warmup, 0)
+    per_step_s = max(1.0, min(10.0, 150.0 / max(total, 1)))
+    rng = np.random.default_rng(777)
+    probe = np.sort(rng.choice(cells, min(cells.size, 64 * threads), replace=False))
+    t0 = time.perf_counter()
+    oracle.simulate_threaded(h, w.cell_size, probe, p, threads=threads, merge=False)
+    rate = probe.size / max(time.perf_counter() - t0, 1e-6)
+    k = int(min(cells.size, max(threads, rate * per_step_s)))
+    steps_done, secs = 0, 0.0
+    for s in range(total):
+        sample = np.sort(rng.choice(cells, k, replace=False))
+        t0 = time.perf_counter()
+        _, _, st = oracle.simulate_threaded(h, w.cell_size, sample, p, threads=threads, merge=False)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            steps_done += st["total_steps"]
+            secs += dt
+    value = steps_done / secs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": R.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded fBm + carved valleys, uint16 dm)",
+            "config": dict(w.describe(), parallelism="host cores"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"per step {k} of {cells.size} release cells, all {w.traj_per_cell} "
+                                       f"particles each (uniform random, seed 777)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = _args()
+    R = Ranks()
+    try:
+        if args.impl == "reference":
+            run_reference(args, R)
+        else:
+            run_awo(args, R)
+    finally:
+        R.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * awo.h -- C ABI of the GB300 avalanche-overlay library (libawo.so).
+ *
+ * The library computes the data-parallel hot path of the avalanche overlay of
+ * "Data-Driven Compute Overlays for Interactive Geographic Simulation and
+ * Visualization" (Komon et al., VIS 2025): per-cell normals and steepness from
+ * a DEM, release-cell selection by a steepness range, Monte-Carlo particle
+ * trajectories that run downslope under persistence, random variation and a
+ * runout-angle stop (Sec. 5.2), and the overlay raster with its mipmap
+ * (Sec. 3).  The paper gives the method in prose; the exact arithmetic each
+ * call performs is stated beside it below.
+ *
+ * Conventions shared by every call:
+ *  - Pointers named d_* are DEVICE pointers on the current CUDA device; the
+ *    caller allocates and owns every buffer.  The library keeps no device
+ *    memory of its own and never allocates.
+ *  - Rasters are row-major, width x height, index y * width + x; cell (x, y)
+ *    has its centre at cell coordinates (u, v) = (x, y).
+ *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
+ *    NULL is the legacy default stream) and returns after enqueueing.
+ *  - Errors are returned as awo_status, never trapped.  Argument checks run
+ *    on the host before anything is enqueued (AWO_EINVAL); a failed launch
+ *    returns AWO_ECUDA.
+ *  - Grids: 1 <= width, height <= 65536, width * height < 2^31,
+ *    cell_size > 0 and finite.
+ *  - Arithmetic is IEEE-754 FP32 with no fused multiply-add in the steps
+ *    marked "exact": results are reproducible bit for bit from the formulas.
+ */
+#ifndef AWO_H
+#define AWO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AWO_OK = 0,
+    AWO_EINVAL = 1,     /* bad argument: null pointer, size, range, alignment */
+    AWO_ENOMEM = 2,     /* workspace smaller than required                    */
+    AWO_ECUDA = 3,      /* a CUDA launch or copy failed                        */
+    AWO_ETIMEOUT = 4,   /* a bounded device wait gave up                       */
+    AWO_EOVERFLOW = 5,  /* a 32-bit count could have wrapped                   */
+    AWO_ECANCELLED = 6  /* work was cancelled before completion                */
+} awo_status;
+
+typedef struct {
+    int32_t width;      /* cells along x (columns)                  */
+    int32_t height;     /* cells along y (rows)                     */
+    float cell_size;    /* metres per cell                          */
+} awo_grid;
+
+/* Trajectory parameters (Sec. 5.2: persistence, random variation, runout
+ * angle, particles per release texel). */
+typedef struct {
+    float mu;             /* tan(runout angle); >= 0                                  */
+    float drag_k;         /* velocity-squared drag per metre; >= 0, drag_k*D < 1      */
+    float persistence;    /* P in [0, 1]: weight of the previous direction            */
+    float randomness;     /* R >= 0: scale of the uniform random variation            */
+    float step_scale;     /* s in (0, 1]: horizontal move in cells; D = s*cell_size m  */
+    float gravity;        /* m/s^2, > 0; used by awo_finalize                          */
+    uint32_t traj_per_cell; /* particles per release cell                             */
+    uint32_t max_steps;   /* moves per particle at most                               */
+    uint64_t seed;        /* Philox key (low word, high word)                         */
+    uint32_t flags;       /* AWO_SIM_* bits below; 0 = accumulate                     */
+    uint32_t reserved;    /* 0                                                        */
+} awo_sim_params;
+
+/* awo_sim_params.flags: clear d_count and d_maxe (cudaMemsetAsync on the
+ * stream) before the particles run, instead of accumulating into them. */
+#define AWO_SIM_CLEAR_OUTPUTS 1u
+
+/* Statistics of one awo_simulate call (device layout, 6 x uint64). */
+typedef struct {
+    uint64_t total_steps; /* recorded moves, summed over particles          */
+    uint64_t n_traj;      /* particles run                                   */
+    uint64_t n_exited;    /* left the sampling domain                        */
+    uint64_t n_capped;    /* reached max_steps                               */
+    uint64_t n_stopped;   /* energy reached zero (or zero direction)         */
+    uint64_t n_rejected;  /* particles skipped: release index >= W*H         */
+} awo_sim_stats;
+
+const char* awo_status_string(awo_status s);
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int32_t awo_version(void);
+
+/*
+ * a0. Decode quantised heights (Sec. 5.2 input DEM; the workloads store
+ * decimetres as uint16):  d_h[i] = (float)d_q[i] * scale  (one rounding, exact).
+ * d_q: uint16 [height*width]; d_h: float [height*width].  scale > 0, finite.
+ */
+awo_status awo_decode_u16(const uint16_t* d_q, awo_grid g, float scale, float* d_h, void* stream);
+
+/*
+ * a1. Normals and steepness (Sec. 5.1/5.2: "compute the surface normals";
+ * release selection evaluates local steepness).  Exact.  For cell (x, y),
+ * with xl = max(x-1, 0), xr = min(x+1, W-1) (same for y):
+ *   gx = (h[y][xr] - h[y][xl]) / (cs * (xr - xl))   (0 when xr == xl)
+ *   gy = (h[yr][x] - h[yl][x]) / (cs * (yr - yl))   (0 when yr == yl)
+ *   tan2 = gx*gx + gy*gy                               (tan^2 of the slope)
+ *   inv = 1 / sqrt(tan2 + 1);  normal = (-gx*inv, -gy*inv, inv)
+ *   slope_deg = atan(sqrt(tan2)) in degrees (NOT exact: within a few ulp).
+ * d_h: float [H*W].  d_normal: float [3*H*W], planes nx, ny, nz (nullable).
+ * d_tan2: float [H*W] (nullable).  d_slope_deg: float [H*W] (nullable).
+ */
+awo_status awo_normals(const float* d_h, awo_grid g, float* d_normal, float* d_tan2,
+                       float* d_slope_deg, void* stream);
+
+/*
+ * b. Release cells (Sec. 5.2: a texel is a potential release point when its
+ * local steepness lies in the user's range; the node outputs a binary map).
+ * Exact.  T = tan(deg * pi / 180)^2 is computed on the host in double and
+ * rounded to float once for each bound; cell i is selected iff
+ * T_lo <= d_tan2[i] <= T_hi.
+ * Outputs: d_mask uint8 [H*W] (0/1, nullable); d_cells uint32 [capacity H*W]:
+ * indices of the selected cells in increasing order; d_n: one uint32, the
+ * number selected.  Requires 0 <= lo_deg <= hi_deg < 90.
+ * Workspace: d_ws of at least awo_release_workspace_bytes(g) bytes, 16-byte
+ * aligned, contents undefined on entry and exit.
+ */
+size_t awo_release_workspace_bytes(awo_grid g);
+awo_status awo_release(const float* d_tan2, awo_grid g, double slope_lo_deg, double slope_hi_deg,
+                       uint8_t* d_mask, uint32_t* d_cells, uint32_t* d_n,
+                       void* d_ws, size_t ws_bytes, void* stream);
+
+/*
+ * c. Particle trajectories (Sec. 5.2, avalanche trajectory node).  Exact.
+ * Runs traj_per_cell particles j = 0..N-1 from every listed release cell and
+ * ACCUMULATES their visits into d_count / d_maxe (so several calls compose;
+ * zero-fill both before the first call, or set AWO_SIM_CLEAR_OUTPUTS).
+ * Particle (cell c, j):
+ *   start: p = centre of c, e = 0, d = g(p) (zero vector on flat ground);
+ *          the start is a visit of c with e = 0.
+ *   move n = 0, 1, ... while n < max_steps:
+ *     footprint of p: i0 = floor(u), j0 = floor(v), fx = u - i0, fy = v - j0,
+ *       i1 = min(i0+1, W-1), j1 = min(j0+1, H-1); heights h00 = h[j0][i0],
+ *       h10 = h[j0][i1], h01 = h[j1][i0], h11 = h[j1][i1]
+ *     z  = (h00*(1-fx) + h10*fx)*(1-fy) + (h01*(1-fx) + h11*fx)*fy
+ *     a  = (h10-h00)*(1-fy) + (h11-h01)*fy;  b = (h01-h00)*(1-fx) + (h11-h10)*fx
+ *     g  = (-a*inv, -b*inv), inv = 1/sqrt(a*a + b*b); g = d when a*a+b*b == 0
+ *     (w0..w3) = Philox4x32-10(counter (c, j, n>>1, 0), key (seed lo, seed hi));
+ *       words (w0, w1) for even n, (w2, w3) for odd n;
+ *       xi = (float)(w >> 8) * 2^-23 - 1   in [-1, 1)
+ *     r  = (P*d + (1-P)*g) + R*xi per component; r == 0 -> stopped
+ *     d  = r * (1/sqrt(r.x*r.x + r.y*r.y));  p' = p + s*d
+ *     p' outside [0, W-1] x [0, H-1] -> exited (not recorded)
+ *     e' = (e - (k*D)*e) + (z - z') - mu*D,  D = s*cs   (k*D, mu*D rounded once)
+ *     e' <= 0 -> stopped (not recorded); else p = p', e = e', and cell
+ *     (i0 + [fx >= 1/2], j0 + [fy >= 1/2]) of p' is visited with e'.
+ *   visit(cell, e): count += 1; maxe = max(maxe, e)
+ * With drag_k = 0, e is the energy-line height: e_n = z_0 - z_n - mu * (path
+ * length), and stopping at e <= 0 is the runout-angle criterion.
+ * d_h: float [H*W].  d_cells: uint32 cell indices (< H*W; a larger index
+ * is skipped on the device and counted in n_rejected).  The number of
+ * release cells is min(*d_n_cells, n_cells_max) when d_n_cells is non-null
+ * (read on the device, so no host sync is needed after awo_release), else
+ * n_cells_max.  d_count: uint32 [H*W], wraps modulo 2^32 (the call is
+ * overflow-free whenever existing counts + n_traj + total_steps < 2^32).
+ * d_maxe: float [H*W], non-negative (metres of energy-line height).
+ * d_stats: awo_sim_stats on the device, overwritten (nullable).
+ * Workspace: at least awo_simulate_workspace_bytes() bytes, 16-byte aligned.
+ */
+size_t awo_simulate_workspace_bytes(void);
+awo_status awo_simulate(const float* d_h, awo_grid g, const uint32_t* d_cells,
+                        const uint32_t* d_n_cells, uint32_t n_cells_max,
+                        const awo_sim_params* p, uint32_t* d_count, float* d_maxe,
+                        awo_sim_stats* d_stats, void* d_ws, size_t ws_bytes, void* stream);
+
+/*
+ * c'. Velocity indicator (Fig. 4: the colour encodes Z^delta_max, read as a
+ * velocity): d_vel[i] = sqrt((2*gravity) * d_maxe[i]).  Exact.
+ * d_vel may alias d_maxe.
+ */
+awo_status awo_finalize(const float* d_maxe, awo_grid g, float gravity, float* d_vel, void* stream);
+
+/*
+ * d. Overlay mipmap (Sec. 3: "from the high-resolution overlay texture, we
+ * then compute a mipmap").  Exact.  Level l+1 has size ceil(W_l/2) x
+ * ceil(H_l/2); its texel (x, y) reduces the texels (2x+dx, 2y+dy),
+ * dx, dy in {0, 1}, that exist in level l: counts are summed and saturated
+ * at 2^32-1, velocities take the maximum.  Level 0 is (d_count, d_vel).
+ * d_count_lv and d_vel_lv are HOST arrays of levels-1 device pointers that
+ * receive levels 1 .. levels-1.  1 <= levels <= 16.
+ */
+awo_status awo_overlay_lod(const uint32_t* d_count, const float* d_vel, awo_grid g, int32_t levels,
+                           uint32_t* const* d_count_lv, float* const* d_vel_lv, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AWO_H */

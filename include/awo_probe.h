@@ -1,0 +1,48 @@
+/*
+ * awo_probe.h -- measurement kernels for the roofline of the particle kernel.
+ *
+ * The particle step of the avalanche workflow (Sec. 5.2) gathers a 2x2
+ * height footprint and scatters two reductions per visit, into rasters that
+ * are L2-resident at the working set of a persistent launch.  The relevant
+ * ceilings are therefore the L2 throughput of scattered 4-byte loads and of
+ * scattered 4-byte reductions, which no vendor table lists.  These kernels
+ * measure them on the running GPU; the caller times each call with CUDA
+ * events on `stream`.  Same conventions as awo.h (caller-owned device
+ * buffers, asynchronous, status codes).
+ */
+#ifndef AWO_PROBE_H
+#define AWO_PROBE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "awo.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * Scattered loads: every thread of a persistent grid performs `iters`
+ * rounds; each round loads 4 independent 4-byte words at hashed positions in
+ * d_buf[0 .. n_words) (n_words a power of two, <= 2^30) and folds them into a
+ * checksum, written to d_sink (one uint32 per thread of the grid, at least
+ * awo_probe_threads() entries).  Loads issued: awo_probe_threads() * iters * 4.
+ */
+awo_status awo_probe_l2_gather(const uint32_t* d_buf, uint32_t n_words, uint32_t iters, uint32_t* d_sink,
+                               void* stream);
+
+/*
+ * Scattered reductions: like the gather probe, but each round issues one
+ * fire-and-forget 32-bit add (RED.ADD) and one 32-bit max (RED.MAX) at hashed
+ * positions of d_buf.  Reductions issued: awo_probe_threads() * iters * 2.
+ */
+awo_status awo_probe_l2_red(uint32_t* d_buf, uint32_t n_words, uint32_t iters, void* stream);
+
+/* Threads of the persistent probe grid on the current device. */
+uint64_t awo_probe_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AWO_PROBE_H */

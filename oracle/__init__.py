@@ -267,3 +267,33 @@ def overlay(h: np.ndarray, cs: float, lo_deg: float, hi_deg: float, params: SimP
     cl, vl = lod(count, vel, levels, precision)
     return {"normals": nrm, "tan2": t2, "slope_deg": sd, "mask": mask, "cells": cells,
             "count": count, "maxe": maxe, "vel": vel, "count_lv": cl, "vel_lv": vl, "stats": st}
+
+
+def simulate_threaded(h: np.ndarray, cs: float, cells: np.ndarray, params: SimParams, threads: int | None = None,
+                      precision: str = "f32", merge: bool = True):
+    """orc_simulate over contiguous chunks of the release list on `threads`
+    host threads (ctypes drops the GIL), each into private rasters; the
+    rasters are merged by sum (counts) and max (energy), which is exactly the
+    single-thread result because both reductions are order-independent."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    threads = max(1, int(threads or os.cpu_count() or 1))
+    cells = np.ascontiguousarray(cells, dtype=np.uint32)
+    chunks = [c for c in np.array_split(cells, threads) if c.size] or [cells]
+    _, npr = _real(precision)
+    h = np.ascontiguousarray(h, dtype=npr)
+
+    def one(c):
+        return simulate(h, cs, c, params, precision,
+                        count64=np.zeros(h.shape, np.uint64), maxe=np.zeros(h.shape, npr))
+
+    with ThreadPoolExecutor(len(chunks)) as ex:
+        parts = list(ex.map(one, chunks))
+    stats = {k: sum(p[2][k] for p in parts) for k in parts[0][2]}
+    if not merge:
+        return None, None, stats
+    count64, maxe = parts[0][0], parts[0][1]
+    for c, m, _ in parts[1:]:
+        count64 += c
+        np.maximum(maxe, m, out=maxe)
+    return count64, maxe, stats

@@ -1,1 +1,245 @@
-"""placeholder"""
+"""GB300 avalanche-overlay hot path: Python binding of ``libawo.so``.
+
+The functions below carry the names of the C ABI in ``include/awo.h`` and do
+argument marshalling only: they check tensor dtypes, devices and sizes, pass
+raw device pointers and the current CUDA stream to the library, and raise
+``AwoError`` on a non-OK status.  Every step of the computation runs in the
+library's CUDA kernels; there is no fallback.  PyTorch supplies device memory
+and streams.
+
+Importing the package does not load the library; the first call does, and it
+raises ``RuntimeError`` when ``libawo.so`` is missing (build it with
+``python -c "import __graft_entry__ as g; g.build()"``).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass, field
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libawo.so")
+
+AWO_OK, AWO_EINVAL, AWO_ENOMEM, AWO_ECUDA, AWO_ETIMEOUT, AWO_EOVERFLOW, AWO_ECANCELLED = range(7)
+
+
+class AwoError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("cell_size", ctypes.c_float)]
+
+    def __repr__(self):
+        return f"Grid({self.width}x{self.height}, {self.cell_size} m)"
+
+    @property
+    def cells(self) -> int:
+        return int(self.width) * int(self.height)
+
+
+class SimParams(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_float), ("drag_k", ctypes.c_float), ("persistence", ctypes.c_float),
+                ("randomness", ctypes.c_float), ("step_scale", ctypes.c_float), ("gravity", ctypes.c_float),
+                ("traj_per_cell", ctypes.c_uint32), ("max_steps", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+    @classmethod
+    def make(cls, mu=math.tan(math.radians(25.0)), drag_k=0.0, persistence=0.9, randomness=0.16,
+             step_scale=1.0, gravity=9.81, traj_per_cell=16, max_steps=1000, seed=0, flags=0):
+        return cls(mu, drag_k, persistence, randomness, step_scale, gravity, traj_per_cell, max_steps,
+                   seed, flags, 0)
+
+
+STATS_FIELDS = ("total_steps", "n_traj", "n_exited", "n_capped", "n_stopped", "n_rejected")
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libawo.so (once) and declares the C prototypes."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: the CUDA library must be built (there is no CPU path)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, u32, f32, f64, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_float,
+                                  ctypes.c_double, ctypes.c_size_t)
+    st = ctypes.c_int
+    protos = {
+        "awo_status_string": (ctypes.c_char_p, [st]),
+        "awo_version": (i32, []),
+        "awo_decode_u16": (st, [vp, Grid, f32, vp, vp]),
+        "awo_normals": (st, [vp, Grid, vp, vp, vp, vp]),
+        "awo_release_workspace_bytes": (sz, [Grid]),
+        "awo_release": (st, [vp, Grid, f64, f64, vp, vp, vp, vp, sz, vp]),
+        "awo_simulate_workspace_bytes": (sz, []),
+        "awo_simulate": (st, [vp, Grid, vp, vp, u32, ctypes.POINTER(SimParams), vp, vp, vp, vp, sz, vp]),
+        "awo_finalize": (st, [vp, Grid, f32, vp, vp]),
+        "awo_overlay_lod": (st, [vp, vp, Grid, i32, vp, vp, vp]),
+        "awo_probe_l2_gather": (st, [vp, u32, u32, vp, vp]),
+        "awo_probe_l2_red": (st, [vp, u32, u32, vp]),
+        "awo_probe_threads": (ctypes.c_uint64, []),
+    }
+    for name, (res, args) in protos.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def status_string(status: int) -> str:
+    return lib().awo_status_string(status).decode()
+
+
+def _check(status: int, what: str):
+    if status != AWO_OK:
+        raise AwoError(status, what)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _dev(t: torch.Tensor | None, dtype, numel: int | None, name: str):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, needs {numel}")
+    return t.data_ptr()
+
+
+def grid(width: int, height: int, cell_size: float) -> Grid:
+    return Grid(int(width), int(height), float(cell_size))
+
+
+# ----------------------------------------------------------------------------
+# The C ABI, one function each
+# ----------------------------------------------------------------------------
+def awo_decode_u16(q: torch.Tensor, g: Grid, scale: float, h: torch.Tensor, stream=None):
+    """q: uint16 heights (an int16 tensor holding the same bits is accepted)."""
+    if q.dtype not in (torch.uint16, torch.int16):
+        raise TypeError("q must be uint16 (or int16 bits)")
+    _check(lib().awo_decode_u16(_dev(q, q.dtype, g.cells, "q"), g, scale,
+                                _dev(h, torch.float32, g.cells, "h"), _stream(stream)), "awo_decode_u16")
+
+
+def awo_normals(h: torch.Tensor, g: Grid, normal=None, tan2=None, slope_deg=None, stream=None):
+    n = g.cells
+    _check(lib().awo_normals(_dev(h, torch.float32, n, "h"), g, _dev(normal, torch.float32, 3 * n, "normal"),
+                             _dev(tan2, torch.float32, n, "tan2"), _dev(slope_deg, torch.float32, n, "slope_deg"),
+                             _stream(stream)), "awo_normals")
+
+
+def awo_release_workspace_bytes(g: Grid) -> int:
+    return int(lib().awo_release_workspace_bytes(g))
+
+
+def awo_release(tan2: torch.Tensor, g: Grid, slope_lo_deg: float, slope_hi_deg: float, mask, cells: torch.Tensor,
+                n: torch.Tensor, ws: torch.Tensor, stream=None):
+    c = g.cells
+    if cells.dtype not in (torch.int32, torch.uint32) or n.dtype not in (torch.int32, torch.uint32):
+        raise TypeError("cells and n must be int32 or uint32")
+    _check(lib().awo_release(_dev(tan2, torch.float32, c, "tan2"), g, slope_lo_deg, slope_hi_deg,
+                             _dev(mask, torch.uint8, c, "mask"), _dev(cells, cells.dtype, c, "cells"),
+                             _dev(n, n.dtype, 1, "n"), _dev(ws, torch.uint8, None, "ws"), ws.numel(),
+                             _stream(stream)), "awo_release")
+
+
+def awo_simulate_workspace_bytes() -> int:
+    return int(lib().awo_simulate_workspace_bytes())
+
+
+def awo_simulate(h: torch.Tensor, g: Grid, cells: torch.Tensor | None, n_cells_dev: torch.Tensor | None,
+                 n_cells_max: int, params: SimParams, count: torch.Tensor, maxe: torch.Tensor,
+                 stats: torch.Tensor | None, ws: torch.Tensor, stream=None):
+    c = g.cells
+    cells_ptr = None
+    if cells is not None:
+        cells_ptr = _dev(cells, cells.dtype, n_cells_max, "cells")
+        if cells.dtype not in (torch.int32, torch.uint32):
+            raise TypeError("cells must be int32 or uint32")
+    ndev = _dev(n_cells_dev, n_cells_dev.dtype, 1, "n_cells_dev") if n_cells_dev is not None else None
+    if count.dtype not in (torch.int32, torch.uint32):
+        raise TypeError("count must be int32 or uint32")
+    count_ptr = _dev(count, count.dtype, c, "count")
+    sp = _dev(stats, torch.int64, 6, "stats") if stats is not None else None
+    _check(lib().awo_simulate(_dev(h, torch.float32, c, "h"), g, cells_ptr, ndev, int(n_cells_max),
+                              ctypes.byref(params), count_ptr, _dev(maxe, torch.float32, c, "maxe"), sp,
+                              _dev(ws, torch.uint8, None, "ws"), ws.numel(), _stream(stream)), "awo_simulate")
+
+
+def awo_finalize(maxe: torch.Tensor, g: Grid, gravity: float, vel: torch.Tensor, stream=None):
+    _check(lib().awo_finalize(_dev(maxe, torch.float32, g.cells, "maxe"), g, gravity,
+                              _dev(vel, torch.float32, g.cells, "vel"), _stream(stream)), "awo_finalize")
+
+
+def lod_shapes(g: Grid, levels: int) -> list[tuple[int, int]]:
+    """(height, width) of levels 0..levels-1."""
+    out = [(int(g.height), int(g.width))]
+    h, w = out[0]
+    for _ in range(1, levels):
+        h, w = (h + 1) // 2, (w + 1) // 2
+        out.append((h, w))
+    return out
+
+
+def awo_overlay_lod(count: torch.Tensor, vel: torch.Tensor, g: Grid, levels: int, count_lv: list, vel_lv: list,
+                    stream=None):
+    shapes = lod_shapes(g, levels)
+    if len(count_lv) != levels - 1 or len(vel_lv) != levels - 1:
+        raise ValueError("count_lv / vel_lv need levels-1 tensors")
+    n = max(levels - 1, 1)
+    cp = (ctypes.c_void_p * n)()
+    vp = (ctypes.c_void_p * n)()
+    for l in range(1, levels):
+        hh, ww = shapes[l]
+        cl, vl = count_lv[l - 1], vel_lv[l - 1]
+        if cl.dtype not in (torch.int32, torch.uint32):
+            raise TypeError("count_lv tensors must be int32 or uint32")
+        cp[l - 1] = _dev(cl, cl.dtype, hh * ww, f"count_lv[{l - 1}]")
+        vp[l - 1] = _dev(vl, torch.float32, hh * ww, f"vel_lv[{l - 1}]")
+    _check(lib().awo_overlay_lod(_dev(count, count.dtype, g.cells, "count"), _dev(vel, torch.float32, g.cells, "vel"),
+                                 g, int(levels), cp if levels > 1 else None, vp if levels > 1 else None,
+                                 _stream(stream)), "awo_overlay_lod")
+
+
+def awo_probe_threads() -> int:
+    return int(lib().awo_probe_threads())
+
+
+def awo_probe_l2_gather(buf: torch.Tensor, iters: int, sink: torch.Tensor, stream=None):
+    _check(lib().awo_probe_l2_gather(_dev(buf, torch.int32, None, "buf"), buf.numel(), int(iters),
+                                     _dev(sink, torch.int32, awo_probe_threads(), "sink"), _stream(stream)),
+           "awo_probe_l2_gather")
+
+
+def awo_probe_l2_red(buf: torch.Tensor, iters: int, stream=None):
+    _check(lib().awo_probe_l2_red(_dev(buf, torch.int32, None, "buf"), buf.numel(), int(iters), _stream(stream)),
+           "awo_probe_l2_red")
+
+
+def stats_dict(stats: torch.Tensor) -> dict:
+    """Host copy of an awo_sim_stats tensor (6 x int64 on the device)."""
+    vals = stats.detach().to("cpu").tolist()
+    return {k: int(v) & 0xFFFFFFFFFFFFFFFF for k, v in zip(STATS_FIELDS, vals)}
+
+
+from .pipeline import Overlay  # noqa: E402  (re-export)

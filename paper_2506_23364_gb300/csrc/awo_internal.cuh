@@ -1,0 +1,45 @@
+// awo_internal.cuh -- helpers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "awo.h"
+
+namespace awo {
+
+// Validates a grid: 1 <= W, H <= 65536, W*H < 2^31, finite positive cell size.
+inline bool grid_ok(awo_grid g)
+{
+    if (g.width < 1 || g.height < 1 || g.width > 65536 || g.height > 65536) return false;
+    if ((int64_t)g.width * (int64_t)g.height >= ((int64_t)1 << 31)) return false;
+    if (!(g.cell_size > 0.0f) || !(g.cell_size < 3.0e38f)) return false;
+    return true;
+}
+
+inline int64_t cells_of(awo_grid g) { return (int64_t)g.width * (int64_t)g.height; }
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Status after enqueueing: any pending launch error becomes AWO_ECUDA.
+inline awo_status launch_status()
+{
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AWO_OK : AWO_ECUDA;
+}
+
+// Number of SMs of the current device (cached per device ordinal).
+int sm_count();
+
+// Grid size for a grid-stride streaming kernel: a multiple of the SM count,
+// capped by the work available.
+inline unsigned stream_blocks(int64_t work_items, int threads, int per_sm = 8)
+{
+    int64_t want = (work_items + threads - 1) / threads;
+    int64_t cap = (int64_t)sm_count() * per_sm;
+    if (want > cap) want = cap;
+    if (want < 1) want = 1;
+    return (unsigned)want;
+}
+
+}  // namespace awo

@@ -1,0 +1,80 @@
+// awo_probe.cu -- L2 scattered-load and scattered-reduction throughput probes.
+//
+// A persistent grid (SMs x 8 blocks of 256 threads, enough warps to cover L2
+// latency) issues independent, hashed 4-byte accesses into a buffer sized by
+// the caller (an L2-resident size gives the L2 ceiling).  The hash is a
+// multiply-xorshift of (thread, round), so accesses spread over all L2
+// slices with no locality between lanes.
+#include "awo_internal.cuh"
+#include "awo_probe.h"
+
+namespace awo {
+
+constexpr int PROBE_THREADS = 256;
+constexpr int PROBE_BLOCKS_PER_SM = 8;
+
+__device__ __forceinline__ uint32_t mix(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+__global__ void __launch_bounds__(PROBE_THREADS) k_probe_gather(const uint32_t* __restrict__ buf, uint32_t mask,
+                                                                uint32_t iters, uint32_t* __restrict__ sink)
+{
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t acc = 0;
+    uint32_t s = mix(tid * 0x9E3779B9u + 1u);
+    for (uint32_t r = 0; r < iters; ++r) {
+        uint32_t a0 = mix(s + 4u * r) & mask;
+        uint32_t a1 = mix(s + 4u * r + 1u) & mask;
+        uint32_t a2 = mix(s + 4u * r + 2u) & mask;
+        uint32_t a3 = mix(s + 4u * r + 3u) & mask;
+        acc += __ldg(buf + a0) ^ __ldg(buf + a1) ^ __ldg(buf + a2) ^ __ldg(buf + a3);
+    }
+    sink[tid] = acc;
+}
+
+__global__ void __launch_bounds__(PROBE_THREADS) k_probe_red(uint32_t* __restrict__ buf, uint32_t mask, uint32_t iters)
+{
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t s = mix(tid * 0x9E3779B9u + 7u);
+    for (uint32_t r = 0; r < iters; ++r) {
+        uint32_t a0 = mix(s + 2u * r) & mask;
+        uint32_t a1 = mix(s + 2u * r + 1u) & mask;
+        atomicAdd(buf + a0, 1u);
+        atomicMax(buf + a1, r);
+    }
+}
+
+}  // namespace awo
+
+using namespace awo;
+
+extern "C" uint64_t awo_probe_threads(void)
+{
+    return (uint64_t)sm_count() * PROBE_BLOCKS_PER_SM * PROBE_THREADS;
+}
+
+static bool pow2_ok(uint32_t n) { return n >= 1024u && n <= (1u << 30) && (n & (n - 1u)) == 0u; }
+
+extern "C" awo_status awo_probe_l2_gather(const uint32_t* d_buf, uint32_t n_words, uint32_t iters, uint32_t* d_sink,
+                                          void* stream)
+{
+    if (!d_buf || !d_sink || !pow2_ok(n_words) || iters == 0) return AWO_EINVAL;
+    k_probe_gather<<<sm_count() * PROBE_BLOCKS_PER_SM, PROBE_THREADS, 0, as_stream(stream)>>>(d_buf, n_words - 1u,
+                                                                                              iters, d_sink);
+    return launch_status();
+}
+
+extern "C" awo_status awo_probe_l2_red(uint32_t* d_buf, uint32_t n_words, uint32_t iters, void* stream)
+{
+    if (!d_buf || !pow2_ok(n_words) || iters == 0) return AWO_EINVAL;
+    k_probe_red<<<sm_count() * PROBE_BLOCKS_PER_SM, PROBE_THREADS, 0, as_stream(stream)>>>(d_buf, n_words - 1u,
+                                                                                           iters);
+    return launch_status();
+}

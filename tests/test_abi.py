@@ -1,0 +1,89 @@
+"""The C-ABI library builds, loads without a GPU, exports every entry point
+that include/*.h declares, and rejects bad arguments on the host before it
+touches the device."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+import paper_2506_23364_gb300 as awo
+from paper_2506_23364_gb300 import build as awo_build
+
+ROOT = os.path.abspath(os.path.join(os.path.dirname(__file__), ".."))
+
+
+@pytest.fixture(scope="module")
+def L():
+    awo_build.build()
+    return awo.lib()
+
+
+def _declared():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(awo_\w+)\s*\(", text))
+    return names
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = _declared()
+    assert {"awo_normals", "awo_release", "awo_simulate", "awo_overlay_lod"} <= names
+    for n in sorted(names):
+        assert hasattr(L, n), n
+
+
+def test_struct_layouts():
+    assert ctypes.sizeof(awo.Grid) == 12
+    assert ctypes.sizeof(awo.SimParams) == 48
+    assert awo.SimParams.seed.offset == 32
+
+
+def test_status_strings_and_version(L):
+    assert awo.status_string(0) == "ok"
+    assert awo.status_string(1) == "invalid argument"
+    assert L.awo_version() >= 10000
+
+
+def test_workspace_sizes(L):
+    assert awo.awo_simulate_workspace_bytes() >= 48
+    g = awo.grid(8192, 8192, 10.0)
+    assert awo.awo_release_workspace_bytes(g) >= 2 * 4 * (8192 * 8192 // 4096)
+    assert awo.awo_release_workspace_bytes(awo.grid(0, 5, 1.0)) == 0
+
+
+@pytest.mark.parametrize("g", [(0, 5, 1.0), (5, 0, 1.0), (70000, 2, 1.0), (65536, 65536, 1.0), (4, 4, 0.0),
+                               (4, 4, float("nan")), (4, 4, -1.0)])
+def test_bad_grids_rejected_on_host(L, g):
+    G = awo.grid(*g)
+    fake = ctypes.c_void_p(16)  # never dereferenced: validation fails first
+    assert L.awo_normals(fake, G, fake, fake, None, None) == awo.AWO_EINVAL
+    assert L.awo_finalize(fake, G, ctypes.c_float(9.81), fake, None) == awo.AWO_EINVAL
+
+
+def test_bad_arguments_rejected_on_host(L):
+    G = awo.grid(16, 16, 10.0)
+    fake = ctypes.c_void_p(256)
+    assert L.awo_normals(None, G, fake, None, None, None) == awo.AWO_EINVAL
+    ws = awo.awo_release_workspace_bytes(G)
+    assert L.awo_release(fake, G, 40.0, 30.0, fake, fake, fake, fake, ws, None) == awo.AWO_EINVAL
+    assert L.awo_release(fake, G, 30.0, 90.0, fake, fake, fake, fake, ws, None) == awo.AWO_EINVAL
+    assert L.awo_release(fake, G, 30.0, 45.0, fake, fake, fake, fake, ws - 1, None) == awo.AWO_ENOMEM
+    assert L.awo_release(fake, G, 30.0, 45.0, fake, fake, fake, ctypes.c_void_p(258), ws, None) == awo.AWO_EINVAL
+    for kw in (dict(persistence=1.5), dict(randomness=-1.0), dict(mu=-0.1), dict(drag_k=0.2),
+               dict(step_scale=0.0), dict(step_scale=2.0), dict(gravity=0.0), dict(flags=2)):
+        p = awo.SimParams.make(**kw)
+        assert L.awo_simulate(fake, G, fake, None, 4, ctypes.byref(p), fake, fake, None, fake, 64,
+                              None) == awo.AWO_EINVAL, kw
+    p = awo.SimParams.make()
+    assert L.awo_simulate(fake, G, fake, None, 4, ctypes.byref(p), fake, fake, None, fake, 8,
+                          None) == awo.AWO_ENOMEM
+    assert L.awo_simulate(fake, G, None, None, 4, ctypes.byref(p), fake, fake, None, fake, 64,
+                          None) == awo.AWO_EINVAL
+    arr = (ctypes.c_void_p * 1)(fake)
+    assert L.awo_overlay_lod(fake, fake, G, 0, arr, arr, None) == awo.AWO_EINVAL
+    assert L.awo_overlay_lod(fake, fake, G, 17, arr, arr, None) == awo.AWO_EINVAL
+    assert L.awo_overlay_lod(fake, fake, G, 2, None, None, None) == awo.AWO_EINVAL
