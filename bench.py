@@ -40,10 +40,18 @@ UNIT = "trajectory-steps/s"
 # read for a release visit.
 ALG_BYTES_PER_VISIT = 24
 
+# Algorithmic lane operations per visit of the particle kernel, counted from
+# the formulas of the move: one Philox4x32-10 block (10 rounds x (2 multiply
+# high + 2 multiply low + 4 xor + 2 key add) = 100) and two uniforms (8);
+# bilinear height 11; gradient and its normalisation 17; direction 17; move
+# and domain test 8; energy and stop test 6; visited cell 5; floors 4.
+ALG_OPS_PER_VISIT = 176
+
 # DRAM bytes per visit of the particle kernel from an ncu capture (dram__bytes
-# read + write), keyed by the SHA-256 of the kernel source it was taken on;
-# a changed kernel reports traffic null until it is captured again.
-DRAM_BYTES_PER_VISIT: dict[str, float] = {}
+# read + write of a 6144^2 crop launch, divided by its visits), keyed by the
+# SHA-256 prefix of the kernel source it was taken on; a changed kernel
+# reports traffic null until it is captured again.
+DRAM_BYTES_PER_VISIT: dict[str, float] = {"fb169e531cc04d53": 321.619456e6 / 1754008332}
 
 
 def _args():
@@ -53,6 +61,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["awo", "reference"], default="awo")
     ap.add_argument("--workload", choices=["large", "mid", "tiny"], default="large")
+    ap.add_argument("--crop", type=int, default=0, help="use the top-left N x N crop of the workload's DEM")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -170,9 +179,10 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # workload
 # ----------------------------------------------------------------------------
-def _workload(name: str):
+def _workload(name: str, crop: int = 0):
     from paper_2506_23364_gb300 import inputs
-    return {"large": inputs.large, "mid": inputs.mid, "tiny": inputs.tiny}[name]()
+    w = {"large": inputs.large, "mid": inputs.mid, "tiny": inputs.tiny}[name]()
+    return inputs.crop(w, crop) if crop else w
 
 
 def _peaks() -> dict:
@@ -210,6 +220,22 @@ def _probe_peaks(torch, awo) -> dict:
     return out
 
 
+def _oracle_rate(oracle, h, cs, cells, p, threads, rng) -> float:
+    """Release cells per second of the threaded oracle, from samples grown
+    until one takes at least a second."""
+    import numpy as np
+
+    k = min(cells.size, 64 * threads)
+    while True:
+        probe = np.sort(rng.choice(cells, k, replace=False))
+        t0 = time.perf_counter()
+        oracle.simulate_threaded(h, cs, probe, p, threads=threads, merge=False)
+        dt = time.perf_counter() - t0
+        if dt >= 1.0 or k >= cells.size:
+            return k / max(dt, 1e-6)
+        k = min(cells.size, int(k * max(2.0, 1.5 / max(dt, 1e-3))))
+
+
 def _cpu_baseline(w, seconds: float, threads: int | None = None) -> dict:
     """The oracle, as it stands, on the host cores over a random sample of the
     workload's release cells (all particles of each sampled cell)."""
@@ -225,10 +251,7 @@ def _cpu_baseline(w, seconds: float, threads: int | None = None) -> dict:
                          max_steps=w.max_steps, seed=w.seed)
     threads = threads or os.cpu_count() or 1
     rng = np.random.default_rng(12345)
-    probe = np.sort(rng.choice(cells, min(cells.size, 64 * threads), replace=False))
-    t0 = time.perf_counter()
-    oracle.simulate_threaded(h, w.cell_size, probe, p, threads=threads, merge=False)
-    rate = probe.size / max(time.perf_counter() - t0, 1e-6)
+    rate = _oracle_rate(oracle, h, w.cell_size, cells, p, threads, rng)
     k = int(min(cells.size, max(threads, rate * seconds)))
     sample = np.sort(rng.choice(cells, k, replace=False))
     t0 = time.perf_counter()
@@ -250,7 +273,7 @@ def run_awo(args, R: Ranks):
 
     import paper_2506_23364_gb300 as awo
 
-    w = _workload(args.workload)
+    w = _workload(args.workload, args.crop)
     params = awo.SimParams.make(mu=w.mu, drag_k=w.drag_k, persistence=w.persistence, randomness=w.randomness,
                                 step_scale=w.step_scale, gravity=w.gravity, traj_per_cell=w.traj_per_cell,
                                 max_steps=w.max_steps, seed=w.seed)
@@ -327,19 +350,29 @@ def run_awo(args, R: Ranks):
 
     peaks = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    alg_bytes = ALG_BYTES_PER_VISIT * visits
-    achieved = alg_bytes / (sim_ms / 1e3) / 1e9
+    sim_s = sim_ms / 1e3
     sha = _kernel_sha()
     traffic = DRAM_BYTES_PER_VISIT.get(sha)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+    # issue / ALU ceiling: 152 SMs x 128 lanes x SM clock (max clock of the run)
+    sms = torch.cuda.get_device_properties(R.device).multi_processor_count
+    mhz = clk.get("sm_max_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = sms * 128 * mhz * 1e6 / 1e12
+    alu_achieved = ALG_OPS_PER_VISIT * visits / sim_s / 1e12
+    roofline = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Tops/s",
+                "frac": alu_achieved / alu_peak,
                 "traffic": traffic * visits if traffic is not None else None, "kernel": "k_simulate",
-                "kernel_ms": sim_ms, "alg_bytes_per_launch": alg_bytes,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
-    l2 = {"gather_loads_per_s": 4 * visits / (sim_ms / 1e3), "red_per_s": 2 * visits / (sim_ms / 1e3),
+                "kernel_ms": sim_ms, "units_per_launch": visits, "alg_ops_per_unit": ALG_OPS_PER_VISIT,
+                "peak_source": f"{sms} SMs x 128 lanes x {mhz:.0f} MHz (issue ceiling; ncu: issue-bound)"}
+    alg_bytes = ALG_BYTES_PER_VISIT * visits
+    roofline_hbm = {"achieved": alg_bytes / sim_s / 1e9, "peak": hbm, "unit": "GB/s",
+                    "frac": alg_bytes / sim_s / 1e9 / hbm, "alg_bytes_per_launch": alg_bytes,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
+    l2 = {"gather_loads_per_s": 4 * visits / sim_s, "red_per_s": 2 * visits / sim_s,
           "probe_l2_gather_loads_per_s": peaks_probe["l2_gather_per_s"],
           "probe_l2_red_per_s": peaks_probe["l2_red_per_s"]}
     l2["gather_frac"] = l2["gather_loads_per_s"] / l2["probe_l2_gather_loads_per_s"]
     l2["red_frac"] = l2["red_per_s"] / l2["probe_l2_red_per_s"]
+    l2["frac_of_binding"] = max(l2["gather_frac"], l2["red_frac"])
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": R.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True, "scaling": "weak",
@@ -353,6 +386,7 @@ def run_awo(args, R: Ranks):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
                     "ms_per_step": e2e_step},
             "gpu_launches": launches_per_step * args.steps, "roofline": roofline, "roofline_l2": l2,
+            "roofline_hbm": roofline_hbm,
             "clocks": clk, "kernel_sha": sha}
     if R.rank == 0 and R.world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(w, args.cpu_seconds)
@@ -369,7 +403,7 @@ def run_reference(args, R: Ranks):
 
     import oracle
 
-    w = _workload(args.workload)
+    w = _workload(args.workload, args.crop)
     h = oracle.decode_u16(w.dem_u16) if w.dem_u16 is not None else w.dem_f32
     _, t2, _ = oracle.normals(h, w.cell_size, want_slope=False)
     _, cells = oracle.release(t2, w.slope_lo_deg, w.slope_hi_deg)
@@ -380,10 +414,7 @@ def run_reference(args, R: Ranks):
     total = args.steps + max(args.warmup, 0)
     per_step_s = max(1.0, min(10.0, 150.0 / max(total, 1)))
     rng = np.random.default_rng(777)
-    probe = np.sort(rng.choice(cells, min(cells.size, 64 * threads), replace=False))
-    t0 = time.perf_counter()
-    oracle.simulate_threaded(h, w.cell_size, probe, p, threads=threads, merge=False)
-    rate = probe.size / max(time.perf_counter() - t0, 1e-6)
+    rate = _oracle_rate(oracle, h, w.cell_size, cells, p, threads, rng)
     k = int(min(cells.size, max(threads, rate * per_step_s)))
     steps_done, secs = 0, 0.0
     for s in range(total):
