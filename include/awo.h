@@ -127,6 +127,30 @@ awo_status awo_release(const float* d_tan2, awo_grid g, double slope_lo_deg, dou
                        void* d_ws, size_t ws_bytes, void* stream);
 
 /*
+ * Release selection without a caller-provided workspace.  (The paper has no
+ * counterpart: this is a library convenience.)  Some callers cannot hand the
+ * library any extra device memory: a plug-in inside a host application, such
+ * as a map renderer, whose allocator owns all device memory; or a real-time
+ * loop that allocates nothing once it has started.  This entry point computes
+ * exactly what awo_release computes, with the same arguments except the
+ * workspace.  Its scratch (two 32-bit words per tile of 4096 cells) lives in
+ * a fixed array of 128 KiB in device memory that the library holds on every
+ * GPU that loads it, until the process exits; the call allocates nothing.
+ *  - Grids of more than AWO_RELEASE_NOALLOC_MAX_CELLS cells (8192 x 8192) are
+ *    rejected with AWO_ENOMEM before anything is enqueued.
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, with that device current); make that first call before any
+ *    stream capture.  A failed lookup returns AWO_ECUDA.
+ *  - Every call uses the same array, which keeps the last call's contents.
+ *    Nothing in it needs to start at zero: each call writes every entry it
+ *    later reads.  Calls that can overlap on the GPU (on different streams,
+ *    or from several host threads) race on the array: serialise them.
+ */
+#define AWO_RELEASE_NOALLOC_MAX_CELLS (8192ll * 8192ll)
+awo_status awo_release_noalloc(const float* d_tan2, awo_grid g, double slope_lo_deg, double slope_hi_deg,
+                               uint8_t* d_mask, uint32_t* d_cells, uint32_t* d_n, void* stream);
+
+/*
  * c. Particle trajectories (Sec. 5.2, avalanche trajectory node).  Exact.
  * Runs traj_per_cell particles j = 0..N-1 from every listed release cell and
  * ACCUMULATES their visits into d_count / d_maxe (so several calls compose;

@@ -79,6 +79,7 @@ def lib() -> ctypes.CDLL:
         "awo_normals": (st, [vp, Grid, vp, vp, vp, vp]),
         "awo_release_workspace_bytes": (sz, [Grid]),
         "awo_release": (st, [vp, Grid, f64, f64, vp, vp, vp, vp, sz, vp]),
+        "awo_release_noalloc": (st, [vp, Grid, f64, f64, vp, vp, vp, vp]),
         "awo_simulate_workspace_bytes": (sz, []),
         "awo_simulate": (st, [vp, Grid, vp, vp, u32, ctypes.POINTER(SimParams), vp, vp, vp, vp, sz, vp]),
         "awo_finalize": (st, [vp, Grid, f32, vp, vp]),
@@ -161,6 +162,28 @@ def awo_release(tan2: torch.Tensor, g: Grid, slope_lo_deg: float, slope_hi_deg: 
                              _dev(mask, torch.uint8, c, "mask"), _dev(cells, cells.dtype, c, "cells"),
                              _dev(n, n.dtype, 1, "n"), _dev(ws, torch.uint8, None, "ws"), ws.numel(),
                              _stream(stream)), "awo_release")
+
+
+RELEASE_NOALLOC_MAX_CELLS = 8192 * 8192
+
+
+def awo_release_noalloc(tan2: torch.Tensor, g: Grid, slope_lo_deg: float, slope_hi_deg: float, mask,
+                        cells: torch.Tensor, n: torch.Tensor, stream=None):
+    """awo_release without a workspace, for callers that cannot hand the
+    library extra device memory (a plug-in whose host application owns the
+    device allocator, a real-time loop that allocates nothing after start-up).
+    The scratch is a fixed 128 KiB array inside the library; grids above
+    RELEASE_NOALLOC_MAX_CELLS cells are refused, and calls that overlap on the
+    GPU race on the shared array."""
+    c = g.cells
+    if c > RELEASE_NOALLOC_MAX_CELLS:
+        raise AwoError(AWO_ENOMEM, f"awo_release_noalloc: grid of {c} cells exceeds the built-in scratch "
+                                   f"limit of {RELEASE_NOALLOC_MAX_CELLS} cells (8192 x 8192)")
+    if cells.dtype not in (torch.int32, torch.uint32) or n.dtype not in (torch.int32, torch.uint32):
+        raise TypeError("cells and n must be int32 or uint32")
+    _check(lib().awo_release_noalloc(_dev(tan2, torch.float32, c, "tan2"), g, slope_lo_deg, slope_hi_deg,
+                                     _dev(mask, torch.uint8, c, "mask"), _dev(cells, cells.dtype, c, "cells"),
+                                     _dev(n, n.dtype, 1, "n"), _stream(stream)), "awo_release_noalloc")
 
 
 def awo_simulate_workspace_bytes() -> int:

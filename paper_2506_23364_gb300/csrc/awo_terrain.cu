@@ -257,3 +257,60 @@ extern "C" awo_status awo_release(const float* d_tan2, awo_grid g, double slope_
     k_release_scatter<<<tiles, RT_THREADS, 0, s>>>(d_tan2, n, t_lo, t_hi, tile_offset, d_cells);
     return launch_status();
 }
+
+// ---------------------------------------------------------------------------
+// Release selection with a scratch array inside the library, for callers that
+// cannot pass a workspace (see awo_release_noalloc in awo.h).  The array holds
+// the tile counts and tile offsets of the three passes for grids up to
+// AWO_RELEASE_NOALLOC_MAX_CELLS cells.
+// ---------------------------------------------------------------------------
+namespace awo {
+
+constexpr int NOALLOC_MAX_TILES = (int)(AWO_RELEASE_NOALLOC_MAX_CELLS / RT_TILE);
+static __device__ __align__(256) uint32_t g_release_scratch[2 * NOALLOC_MAX_TILES];
+
+// Device address of g_release_scratch for the current device.  In host code
+// the symbol name is only a host-side stand-in, so the address is looked up
+// once per device with cudaGetSymbolAddress while that device is current.
+static awo_status noalloc_scratch(uint32_t** out)
+{
+    static std::mutex mu;
+    static std::vector<uint32_t*> addr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return AWO_ECUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)addr.size() <= dev) addr.resize(dev + 1, nullptr);
+    if (addr[dev] == nullptr) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_release_scratch) != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            return AWO_ECUDA;
+        }
+        addr[dev] = static_cast<uint32_t*>(p);
+    }
+    *out = addr[dev];
+    return AWO_OK;
+}
+
+}  // namespace awo
+
+extern "C" awo_status awo_release_noalloc(const float* d_tan2, awo_grid g, double slope_lo_deg, double slope_hi_deg,
+                                          uint8_t* d_mask, uint32_t* d_cells, uint32_t* d_n, void* stream)
+{
+    if (!d_tan2 || !d_cells || !d_n || !grid_ok(g)) return AWO_EINVAL;
+    if (!(slope_lo_deg >= 0.0) || !(slope_hi_deg < 90.0) || slope_lo_deg > slope_hi_deg) return AWO_EINVAL;
+    const int64_t n = cells_of(g);
+    if (n > AWO_RELEASE_NOALLOC_MAX_CELLS) return AWO_ENOMEM;
+    uint32_t* scratch = nullptr;
+    awo_status st = noalloc_scratch(&scratch);
+    if (st != AWO_OK) return st;
+    const int tiles = (int)((n + RT_TILE - 1) / RT_TILE);
+    uint32_t* tile_count = scratch;
+    uint32_t* tile_offset = scratch + NOALLOC_MAX_TILES;
+    const float t_lo = tan2_of_degrees(slope_lo_deg), t_hi = tan2_of_degrees(slope_hi_deg);
+    cudaStream_t s = as_stream(stream);
+    k_release_mask<<<tiles, RT_THREADS, 0, s>>>(d_tan2, n, t_lo, t_hi, d_mask, tile_count);
+    k_release_scan<<<1, 1024, 0, s>>>(tile_count, tiles, tile_offset, d_n);
+    k_release_scatter<<<tiles, RT_THREADS, 0, s>>>(d_tan2, n, t_lo, t_hi, tile_offset, d_cells);
+    return launch_status();
+}
