@@ -81,12 +81,14 @@ class Ranks:
         self.local = int(os.environ.get("LOCAL_RANK", "0"))
         self.dist = dist if self.world > 1 else None
         self.torch = torch
+        backend = None
         if self.dist is not None:
-            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            backend = os.environ.get("AWO_DIST_BACKEND") or ("nccl" if torch.cuda.is_available() else "gloo")
             if backend == "nccl":
                 torch.cuda.set_device(self.local)
             dist.init_process_group(backend)
-        self.device = torch.device("cuda", self.local) if torch.cuda.is_available() else torch.device("cpu")
+        on_gpu = torch.cuda.is_available() and (self.dist is None or backend == "nccl")
+        self.device = torch.device("cuda", self.local) if on_gpu else torch.device("cpu")
 
     def barrier(self):
         if self.dist is not None:
