@@ -185,9 +185,11 @@ awo_status awo_release_noalloc(const float* d_tan2, awo_grid g, double slope_lo_
  * overflow-free whenever existing counts + n_traj + total_steps < 2^32).
  * d_maxe: float [H*W], non-negative (metres of energy-line height).
  * d_stats: awo_sim_stats on the device, overwritten (nullable).
- * Workspace: at least awo_simulate_workspace_bytes() bytes, 16-byte aligned.
+ * Workspace: at least awo_simulate_workspace_bytes(n_cells_max) bytes,
+ * 16-byte aligned (a work counter, the statistics, and a 16-byte start
+ * record per release cell); contents undefined on entry and exit.
  */
-size_t awo_simulate_workspace_bytes(void);
+size_t awo_simulate_workspace_bytes(uint32_t n_cells_max);
 awo_status awo_simulate(const float* d_h, awo_grid g, const uint32_t* d_cells,
                         const uint32_t* d_n_cells, uint32_t n_cells_max,
                         const awo_sim_params* p, uint32_t* d_count, float* d_maxe,

@@ -80,7 +80,7 @@ def lib() -> ctypes.CDLL:
         "awo_release_workspace_bytes": (sz, [Grid]),
         "awo_release": (st, [vp, Grid, f64, f64, vp, vp, vp, vp, sz, vp]),
         "awo_release_noalloc": (st, [vp, Grid, f64, f64, vp, vp, vp, vp]),
-        "awo_simulate_workspace_bytes": (sz, []),
+        "awo_simulate_workspace_bytes": (sz, [u32]),
         "awo_simulate": (st, [vp, Grid, vp, vp, u32, ctypes.POINTER(SimParams), vp, vp, vp, vp, sz, vp]),
         "awo_finalize": (st, [vp, Grid, f32, vp, vp]),
         "awo_overlay_lod": (st, [vp, vp, Grid, i32, vp, vp, vp]),
@@ -186,8 +186,8 @@ def awo_release_noalloc(tan2: torch.Tensor, g: Grid, slope_lo_deg: float, slope_
                                      _dev(n, n.dtype, 1, "n"), _stream(stream)), "awo_release_noalloc")
 
 
-def awo_simulate_workspace_bytes() -> int:
-    return int(lib().awo_simulate_workspace_bytes())
+def awo_simulate_workspace_bytes(n_cells_max: int) -> int:
+    return int(lib().awo_simulate_workspace_bytes(int(n_cells_max)))
 
 
 def awo_simulate(h: torch.Tensor, g: Grid, cells: torch.Tensor | None, n_cells_dev: torch.Tensor | None,

@@ -1,22 +1,31 @@
 // awo_simulate.cu -- Monte-Carlo avalanche trajectories (Sec. 5.2).
 //
 // Design (GB300):
-//  * Persistent kernel, one lane per particle.  Each warp takes chunks of
-//    consecutive work items (item t = release-list index * N + j) from a
-//    global counter and refills a lane as soon as its particle ends, so lanes
-//    never idle behind a long particle of the same warp.  Consecutive items
-//    are particles of the same or neighbouring release cells, so the lanes of
-//    a warp, and the warps in flight, touch a compact region of the DEM and
-//    the rasters (it stays L2-resident even when the DEM does not).
-//  * The loop body is the same for a fresh particle and a moving one: gather
-//    the 4-texel footprint at the current position, account for the move that
-//    arrived there (or for the release visit), then draw and move.  New and
-//    old lanes of a warp therefore execute one instruction stream.
-//  * Visits go to the rasters with fire-and-forget reductions (RED.ADD on the
-//    count, RED.MAX on the float bits of the non-negative energy); lanes of a
-//    warp that hit the same cell are merged first (__match_any_sync), which
-//    removes most reductions in the first moves, when all particles of a cell
-//    are still together.
+//  * Persistent kernel, one lane per particle.  A warp takes a few release
+//    cells at a time from a global counter (one atomic per cell group) and
+//    walks their particles (cell-major, particle j minor) with a warp-uniform
+//    cursor; a lane is refilled the moment its particle ends, so lanes never
+//    idle behind a long particle of the same warp.  The particles in flight
+//    come from a compact window of the release list, so the lanes of a warp,
+//    and the warps of the GPU, touch a compact region of the DEM and of the
+//    rasters, which stays L2-resident even when the DEM does not.
+//  * No integer division on the refill path: the cursor carries (cell, j),
+//    and a cell index becomes (x, y) through a float reciprocal of W and one
+//    exact correction step.
+//  * A particle starts at refill time: the 2x2 footprint of its release cell
+//    is gathered and its release visit recorded (merged over the particles of
+//    the cell that start together).  Each loop iteration is then exactly one
+//    move and its visit -- direction from the footprint kept in registers,
+//    draw, step, footprint and energy at the new position, record -- written
+//    without data-dependent branches except the merged record, so a warp runs
+//    one instruction stream.
+//  * Visits go to the rasters as fire-and-forget reductions (RED.ADD on the
+//    count, RED.MAX on the bits of the non-negative energy); lanes of a warp
+//    that hit the same cell are merged first (__match_any_sync), which
+//    removes nearly all reductions while the particles of a cell still move
+//    together.
+//  * Philox4x32-10 round keys are computed once on the host and read from the
+//    kernel's parameter bank.
 //  * Arithmetic is FP32 with explicit round-to-nearest intrinsics: no fused
 //    multiply-add, IEEE sqrt and reciprocal, so every particle follows the
 //    formulas of awo.h bit for bit.
@@ -25,11 +34,21 @@
 namespace awo {
 
 struct SimWorkspace {
-    unsigned long long next_item;  // global work counter
+    unsigned long long next_cell;  // global work counter, in release-list entries
     unsigned long long total_steps, n_traj, n_exited, n_capped, n_stopped, n_rejected;
     unsigned long long pad;
 };
 static_assert(sizeof(SimWorkspace) == 64, "workspace layout");
+
+// Start of the particles of one release cell, shared by all N of them:
+// position, height and initial direction (the steepest descent at the cell
+// centre, zero on flat ground).  xy = x | y << 16; xy = ~0u marks an index
+// outside the grid.
+struct __align__(16) CellStart {
+    uint32_t xy;
+    float z0, d0x, d0y;
+};
+static_assert(sizeof(CellStart) == 16, "start record layout");
 
 struct SimArgs {
     const float* h;
@@ -38,30 +57,32 @@ struct SimArgs {
     uint32_t n_cells_max;
     int W, H;
     uint32_t n_grid;       // W*H
+    float invW;            // 1/W rounded, for the cell -> (x, y) split
     float Wm1, Hm1;        // W-1, H-1 as floats (exact for W, H <= 2^24)
     float P, oneP, R, s;   // persistence, 1-P, randomness, step in cells
     float kD, muD;         // drag_k*D, mu*D  (D = s*cell_size)
     uint32_t N, max_steps;
-    uint32_t key0, key1;
+    uint32_t cells_per_fetch;
+    uint32_t rk0[10], rk1[10];  // Philox round keys
     uint32_t* count;
     float* maxe;
     SimWorkspace* ws;
+    CellStart* starts;     // one per release-list entry
 };
 
 constexpr int SIM_THREADS = 256;
-constexpr uint32_t SIM_CHUNK = 256;  // items per global fetch
+constexpr uint32_t SIM_FETCH_ITEMS = 256;  // particles per global fetch, at least
 
 // Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64 products
-// of the even words, word permutation with key injection, Weyl key bumps.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+// of the even words and a word permutation that mixes in the round key.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint32_t* __restrict__ rk0,
+                                               const uint32_t* __restrict__ rk1)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
         uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
+        c = make_uint4(hi1 ^ c.y ^ rk0[r], lo1, hi0 ^ c.w ^ rk1[r], lo0);
     }
     return c;
 }
@@ -84,40 +105,21 @@ __device__ __forceinline__ Foot gather(const float* __restrict__ h, int W, int H
     f.j0 = __float2int_rd(v);
     f.fx = __fsub_rn(u, __int2float_rn(f.i0));
     f.fy = __fsub_rn(v, __int2float_rn(f.j0));
-    int i1 = min(f.i0 + 1, W - 1);
-    int j1 = min(f.j0 + 1, H - 1);
-    const float* r0 = h + (size_t)f.j0 * (size_t)W;
-    const float* r1 = h + (size_t)j1 * (size_t)W;
-    f.h00 = __ldg(r0 + f.i0);
-    f.h10 = __ldg(r0 + i1);
-    f.h01 = __ldg(r1 + f.i0);
-    f.h11 = __ldg(r1 + i1);
+    const int di = f.i0 + 1 < W ? 1 : 0;
+    const size_t dj = f.j0 + 1 < H ? (size_t)W : 0;
+    const float* p = h + (size_t)f.j0 * (size_t)W + f.i0;
+    f.h00 = __ldg(p);
+    f.h10 = __ldg(p + di);
+    f.h01 = __ldg(p + dj);
+    f.h11 = __ldg(p + dj + di);
     return f;
 }
 
-__device__ __forceinline__ float bilinear(const Foot& f)
+__device__ __forceinline__ float bilinear(const Foot& f, float ox, float oy)
 {
-    float ox = __fsub_rn(1.0f, f.fx), oy = __fsub_rn(1.0f, f.fy);
     float top = __fadd_rn(__fmul_rn(f.h00, ox), __fmul_rn(f.h10, f.fx));
     float bot = __fadd_rn(__fmul_rn(f.h01, ox), __fmul_rn(f.h11, f.fx));
     return __fadd_rn(__fmul_rn(top, oy), __fmul_rn(bot, f.fy));
-}
-
-// Steepest descent of the bilinear patch; fallback (fbx, fby) when flat.
-__device__ __forceinline__ void downslope(const Foot& f, float fbx, float fby, float& gx, float& gy)
-{
-    float ox = __fsub_rn(1.0f, f.fx), oy = __fsub_rn(1.0f, f.fy);
-    float a = __fadd_rn(__fmul_rn(__fsub_rn(f.h10, f.h00), oy), __fmul_rn(__fsub_rn(f.h11, f.h01), f.fy));
-    float b = __fadd_rn(__fmul_rn(__fsub_rn(f.h01, f.h00), ox), __fmul_rn(__fsub_rn(f.h11, f.h10), f.fx));
-    float n2 = __fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b));
-    if (n2 == 0.0f) {
-        gx = fbx;
-        gy = fby;
-    } else {
-        float inv = __frcp_rn(__fsqrt_rn(n2));
-        gx = __fmul_rn(-a, inv);
-        gy = __fmul_rn(-b, inv);
-    }
 }
 
 // Merged visit of the lanes in `active` that record (idx, e).  Lanes with the
@@ -130,147 +132,207 @@ __device__ __forceinline__ void record(uint32_t* __restrict__ count, float* __re
 {
     unsigned grp = __match_any_sync(active, idx);
     unsigned emax = __reduce_max_sync(grp, __float_as_uint(e));
-    int lane = threadIdx.x & 31;
-    if (lane == __ffs(grp) - 1) {
+    if ((threadIdx.x & 31) == (unsigned)(__ffs(grp) - 1)) {
         atomicAdd(count + idx, (unsigned)__popc(grp));
         if (emax != 0u) atomicMax(reinterpret_cast<unsigned*>(maxe) + idx, emax);
     }
 }
 
-__global__ void __launch_bounds__(SIM_THREADS) k_simulate(SimArgs a)
+// Advances a (cell, j) cursor by k <= 32 particles of N per cell.
+__device__ __forceinline__ void advance(uint32_t& ci, uint32_t& j, uint32_t k, uint32_t N)
+{
+    j += k;
+    if (j >= N) {
+        if (N >= 32u) {
+            j -= N;
+            ci += 1u;
+        } else {
+            uint32_t q = j / N;
+            ci += q;
+            j -= q * N;
+        }
+    }
+}
+
+// Prologue: per release-list entry, the start record and the release visit
+// of all N particles (count += N; their energy is 0, so the maximum is
+// unchanged).  Grid-stride over the entries, whose number may be on the device.
+__global__ void __launch_bounds__(256) k_sim_starts(const __grid_constant__ SimArgs a)
+{
+    uint32_t n_cells = a.n_cells_max;
+    if (a.n_cells_dev) n_cells = min(n_cells, *a.n_cells_dev);
+    for (uint32_t ci = blockIdx.x * blockDim.x + threadIdx.x; ci < n_cells; ci += gridDim.x * blockDim.x) {
+        const uint32_t cell = __ldg(a.cells + ci);
+        CellStart st;
+        if (cell < a.n_grid) {
+            const int y = (int)(cell / (uint32_t)a.W);
+            const int x = (int)(cell - (uint32_t)y * (uint32_t)a.W);
+            const Foot f = gather(a.h, a.W, a.H, __int2float_rn(x), __int2float_rn(y));
+            const float ox = __fsub_rn(1.0f, f.fx), oy = __fsub_rn(1.0f, f.fy);
+            const float ga = __fadd_rn(__fmul_rn(__fsub_rn(f.h10, f.h00), oy), __fmul_rn(__fsub_rn(f.h11, f.h01), f.fy));
+            const float gb = __fadd_rn(__fmul_rn(__fsub_rn(f.h01, f.h00), ox), __fmul_rn(__fsub_rn(f.h11, f.h10), f.fx));
+            const float gn2 = __fadd_rn(__fmul_rn(ga, ga), __fmul_rn(gb, gb));
+            st.xy = (uint32_t)x | ((uint32_t)y << 16);
+            st.z0 = bilinear(f, ox, oy);
+            st.d0x = 0.0f;
+            st.d0y = 0.0f;
+            if (gn2 != 0.0f) {
+                const float inv = __frcp_rn(__fsqrt_rn(gn2));
+                st.d0x = __fmul_rn(-ga, inv);
+                st.d0y = __fmul_rn(-gb, inv);
+            }
+            atomicAdd(a.count + cell, a.N);
+        } else {
+            st.xy = ~0u;
+            st.z0 = st.d0x = st.d0y = 0.0f;
+        }
+        a.starts[ci] = st;
+    }
+}
+
+__global__ void __launch_bounds__(SIM_THREADS) k_simulate(const __grid_constant__ SimArgs a)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lane_lt = (1u << lane) - 1u;
 
-    uint64_t n_cells = a.n_cells_max;
-    if (a.n_cells_dev) {
-        uint32_t nd = *a.n_cells_dev;
-        if (nd < n_cells) n_cells = nd;
-    }
-    const uint64_t total = n_cells * (uint64_t)a.N;
+    uint32_t n_cells = a.n_cells_max;
+    if (a.n_cells_dev) n_cells = min(n_cells, *a.n_cells_dev);
 
-    // warp-uniform chunk of items
-    uint64_t chunk_next = 0, chunk_end = 0;
-    bool exhausted = (total == 0);
+    // warp-uniform cursor over (release-list entry, particle) and the end of
+    // the current cell group
+    uint32_t cur_ci = 0, cur_j = 0, end_ci = 0;
+    bool exhausted = (n_cells == 0u);
 
-    // lane state
+    // lane state: position, its footprint and height, direction, energy,
+    // recorded moves n (n == 0 only before the first move, when the footprint
+    // registers are not used)
     bool live = false;
-    bool fresh = false;
     uint32_t cell = 0, j = 0, n = 0;
-    float u = 0.f, v = 0.f, dx = 0.f, dy = 0.f, e = 0.f, z = 0.f;
+    float u = 0.f, v = 0.f, z = 0.f, dx = 0.f, dy = 0.f, e = 0.f;
+    float fx = 0.f, fy = 0.f, h00 = 0.f, h10 = 0.f, h01 = 0.f, h11 = 0.f;
 
     unsigned long long my_steps = 0;
     unsigned my_traj = 0, my_exit = 0, my_cap = 0, my_stop = 0, my_bad = 0;
 
     while (true) {
-        // ---- refill idle lanes from the warp's chunk --------------------
+        // ---- refill idle lanes: start particles at their release cell -------
         unsigned idle = __ballot_sync(0xffffffffu, !live);
         while (idle != 0u && !exhausted) {
-            if (chunk_next == chunk_end) {
+            if (cur_ci >= end_ci) {
                 unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(&a.ws->next_item, (unsigned long long)SIM_CHUNK);
+                if (lane == 0) base = atomicAdd(&a.ws->next_cell, (unsigned long long)a.cells_per_fetch);
                 base = __shfl_sync(0xffffffffu, base, 0);
-                if (base >= total) {
+                if (base >= n_cells) {
                     exhausted = true;
                     break;
                 }
-                chunk_next = base;
-                chunk_end = base + SIM_CHUNK < total ? base + SIM_CHUNK : total;
+                cur_ci = (uint32_t)base;
+                cur_j = 0;
+                end_ci = (uint32_t)min((unsigned long long)n_cells, base + a.cells_per_fetch);
             }
-            unsigned avail = (unsigned)(chunk_end - chunk_next);
+            // particles left in the group (capped at 32)
+            unsigned long long left = (unsigned long long)(end_ci - cur_ci) * a.N - cur_j;
+            unsigned avail = left < 32ull ? (unsigned)left : 32u;
             unsigned want = (unsigned)__popc(idle);
             unsigned take = want < avail ? want : avail;
             unsigned rank = (unsigned)__popc(idle & lane_lt);
             if (((idle >> lane) & 1u) && rank < take) {
-                uint64_t t = chunk_next + rank;
-                uint64_t ci = t / a.N;
-                j = (uint32_t)(t - ci * a.N);
-                cell = __ldg(a.cells + ci);
-                if (cell < a.n_grid) {
-                    u = __int2float_rn((int)(cell % (uint32_t)a.W));
-                    v = __int2float_rn((int)(cell / (uint32_t)a.W));
+                uint32_t ci = cur_ci, jj = cur_j;
+                advance(ci, jj, rank, a.N);
+                const uint4 st = __ldg(reinterpret_cast<const uint4*>(a.starts) + ci);
+                if (st.x != ~0u) {
+                    cell = (st.x >> 16) * (uint32_t)a.W + (st.x & 0xffffu);
+                    j = jj;
+                    u = __int2float_rn((int)(st.x & 0xffffu));
+                    v = __int2float_rn((int)(st.x >> 16));
+                    z = __uint_as_float(st.y);
+                    dx = __uint_as_float(st.z);
+                    dy = __uint_as_float(st.w);
                     n = 0;
                     e = 0.f;
-                    dx = 0.f;
-                    dy = 0.f;
-                    live = true;
-                    fresh = true;
+                    if (a.max_steps == 0u) {
+                        ++my_cap;  // capped at the release visit
+                        ++my_traj;
+                    } else {
+                        live = true;
+                    }
                 } else {
                     ++my_bad;  // release index outside the grid: skipped, reported
                 }
             }
-            chunk_next += take;
+            advance(cur_ci, cur_j, take, a.N);
             idle = __ballot_sync(0xffffffffu, !live);
         }
-        unsigned active = __ballot_sync(0xffffffffu, live);
+        const unsigned active = __ballot_sync(0xffffffffu, live);
         if (active == 0u) break;
         if (!live) continue;
 
-        // ---- footprint at the current position ------------------------
-        Foot f = gather(a.h, a.W, a.H, u, v);
-        float z1 = bilinear(f);
-        bool alive = true;
-        uint32_t vidx = (uint32_t)(f.j0 + (f.fy >= 0.5f ? 1 : 0)) * (uint32_t)a.W + (uint32_t)(f.i0 + (f.fx >= 0.5f ? 1 : 0));
-        bool moved = !fresh;
-        if (moved) {
-            // energy of the move that arrived here
-            float e1 = __fsub_rn(__fadd_rn(__fsub_rn(e, __fmul_rn(a.kD, e)), __fsub_rn(z, z1)), a.muD);
-            if (!(e1 > 0.0f)) {
-                alive = false;  // stopped before this position: not recorded
-                ++my_stop;
-                ++my_traj;
-            } else {
-                e = e1;
-                ++n;
-                ++my_steps;
-            }
-        }
-        // visits: the release cell (e = 0, count only) or the new position
-        unsigned rec = __ballot_sync(active, alive);
-        if (alive) record(a.count, a.maxe, rec, vidx, e);  // e == 0 on the release visit
+        // ---- one move: direction at p, draw, step, energy at p' ------------
+        const float ox = __fsub_rn(1.0f, fx), oy = __fsub_rn(1.0f, fy);
+        // steepest descent of the bilinear patch at p; the previous direction
+        // when flat (d = 0 before the first move)
+        const float ga = __fadd_rn(__fmul_rn(__fsub_rn(h10, h00), oy), __fmul_rn(__fsub_rn(h11, h01), fy));
+        const float gb = __fadd_rn(__fmul_rn(__fsub_rn(h01, h00), ox), __fmul_rn(__fsub_rn(h11, h10), fx));
+        const float gn2 = __fadd_rn(__fmul_rn(ga, ga), __fmul_rn(gb, gb));
+        const float ginv = __frcp_rn(__fsqrt_rn(gn2));
+        // before the first move d holds d_0 = g(p_0) from the start record,
+        // which is also the steepest descent at p_0
+        const bool keep = (gn2 == 0.0f) || (n == 0u);
+        const float gx = keep ? dx : __fmul_rn(-ga, ginv);
+        const float gy = keep ? dy : __fmul_rn(-gb, ginv);
+        const float px = dx, py = dy;
 
-        if (alive && n == a.max_steps) {
-            alive = false;
-            ++my_cap;
-            ++my_traj;
-        }
-        if (alive) {
-            float gx, gy;
-            downslope(f, fresh ? 0.0f : dx, fresh ? 0.0f : dy, gx, gy);
-            if (fresh) {
-                dx = gx;
-                dy = gy;
+        const uint4 w = philox4x32_10(make_uint4(cell, j, n >> 1, 0u), a.rk0, a.rk1);
+        const bool odd = (n & 1u) != 0u;
+        const float xix = uniform_pm1(odd ? w.z : w.x);
+        const float xiy = uniform_pm1(odd ? w.w : w.y);
+        const float rx = __fadd_rn(__fadd_rn(__fmul_rn(a.P, px), __fmul_rn(a.oneP, gx)), __fmul_rn(a.R, xix));
+        const float ry = __fadd_rn(__fadd_rn(__fmul_rn(a.P, py), __fmul_rn(a.oneP, gy)), __fmul_rn(a.R, xiy));
+        const float r2 = __fadd_rn(__fmul_rn(rx, rx), __fmul_rn(ry, ry));
+        const float rinv = __frcp_rn(__fsqrt_rn(r2));
+        const bool zero_dir = (r2 == 0.0f);
+        const float ndx = __fmul_rn(rx, rinv), ndy = __fmul_rn(ry, rinv);
+        const float u1 = __fadd_rn(u, __fmul_rn(a.s, ndx));
+        const float v1 = __fadd_rn(v, __fmul_rn(a.s, ndy));
+        const bool inside = !zero_dir && u1 >= 0.0f && u1 <= a.Wm1 && v1 >= 0.0f && v1 <= a.Hm1;
+
+        // footprint at p' (at p when p' is outside, so every load stays in the grid)
+        const Foot f = gather(a.h, a.W, a.H, inside ? u1 : u, inside ? v1 : v);
+        const float z1 = bilinear(f, __fsub_rn(1.0f, f.fx), __fsub_rn(1.0f, f.fy));
+        const float e1 = __fsub_rn(__fadd_rn(__fsub_rn(e, __fmul_rn(a.kD, e)), __fsub_rn(z, z1)), a.muD);
+        const bool moved = inside && e1 > 0.0f;
+
+        const unsigned rec = __ballot_sync(active, moved);
+        if (moved) {
+            const uint32_t vidx = (uint32_t)(f.j0 + (f.fy >= 0.5f ? 1 : 0)) * (uint32_t)a.W +
+                                  (uint32_t)(f.i0 + (f.fx >= 0.5f ? 1 : 0));
+            record(a.count, a.maxe, rec, vidx, e1);
+            u = u1;
+            v = v1;
+            z = z1;
+            e = e1;
+            dx = ndx;
+            dy = ndy;
+            fx = f.fx;
+            fy = f.fy;
+            h00 = f.h00;
+            h10 = f.h10;
+            h01 = f.h01;
+            h11 = f.h11;
+            ++n;
+            ++my_steps;
+            if (n == a.max_steps) {
+                live = false;
+                ++my_cap;
             }
-            uint4 w = philox4x32_10(make_uint4(cell, j, n >> 1, 0u), a.key0, a.key1);
-            uint32_t wx = (n & 1u) ? w.z : w.x;
-            uint32_t wy = (n & 1u) ? w.w : w.y;
-            float xix = uniform_pm1(wx), xiy = uniform_pm1(wy);
-            float rx = __fadd_rn(__fadd_rn(__fmul_rn(a.P, dx), __fmul_rn(a.oneP, gx)), __fmul_rn(a.R, xix));
-            float ry = __fadd_rn(__fadd_rn(__fmul_rn(a.P, dy), __fmul_rn(a.oneP, gy)), __fmul_rn(a.R, xiy));
-            float r2 = __fadd_rn(__fmul_rn(rx, rx), __fmul_rn(ry, ry));
-            if (r2 == 0.0f) {
-                alive = false;
-                ++my_stop;
-                ++my_traj;
-            } else {
-                float inv = __frcp_rn(__fsqrt_rn(r2));
-                dx = __fmul_rn(rx, inv);
-                dy = __fmul_rn(ry, inv);
-                float u1 = __fadd_rn(u, __fmul_rn(a.s, dx));
-                float v1 = __fadd_rn(v, __fmul_rn(a.s, dy));
-                if (!(u1 >= 0.0f && u1 <= a.Wm1 && v1 >= 0.0f && v1 <= a.Hm1)) {
-                    alive = false;
-                    ++my_exit;
-                    ++my_traj;
-                } else {
-                    u = u1;
-                    v = v1;
-                    z = z1;
-                }
-            }
+        } else {
+            live = false;
+            if (inside || zero_dir)
+                ++my_stop;  // energy exhausted (or no direction): not recorded
+            else
+                ++my_exit;
         }
-        fresh = false;
-        live = alive;
+        if (!live) ++my_traj;
     }
 
     // ---- statistics -----------------------------------------------------
@@ -328,7 +390,12 @@ static bool params_ok(const awo_sim_params* p, float cs)
 
 using namespace awo;
 
-extern "C" size_t awo_simulate_workspace_bytes(void) { return sizeof(SimWorkspace); }
+static size_t starts_offset() { return 256; }
+
+extern "C" size_t awo_simulate_workspace_bytes(uint32_t n_cells_max)
+{
+    return starts_offset() + (size_t)n_cells_max * sizeof(CellStart);
+}
 
 extern "C" awo_status awo_simulate(const float* d_h, awo_grid g, const uint32_t* d_cells, const uint32_t* d_n_cells,
                                    uint32_t n_cells_max, const awo_sim_params* p, uint32_t* d_count, float* d_maxe,
@@ -339,7 +406,7 @@ extern "C" awo_status awo_simulate(const float* d_h, awo_grid g, const uint32_t*
     if (!params_ok(p, g.cell_size)) return AWO_EINVAL;
     if ((((uintptr_t)d_ws) & 15u) != 0 || (((uintptr_t)d_count) & 3u) != 0 || (((uintptr_t)d_maxe) & 3u) != 0)
         return AWO_EINVAL;
-    if (ws_bytes < sizeof(SimWorkspace)) return AWO_ENOMEM;
+    if (ws_bytes < awo_simulate_workspace_bytes(n_cells_max)) return AWO_ENOMEM;
     cudaStream_t s = as_stream(stream);
     SimWorkspace* ws = static_cast<SimWorkspace*>(d_ws);
     if (cudaMemsetAsync(ws, 0, sizeof(SimWorkspace), s) != cudaSuccess) return AWO_ECUDA;
@@ -359,6 +426,7 @@ extern "C" awo_status awo_simulate(const float* d_h, awo_grid g, const uint32_t*
     a.W = g.width;
     a.H = g.height;
     a.n_grid = (uint32_t)cells_of(g);
+    a.invW = 1.0f / (float)g.width;
     a.Wm1 = (float)(g.width - 1);
     a.Hm1 = (float)(g.height - 1);
     a.P = p->persistence;
@@ -369,13 +437,22 @@ extern "C" awo_status awo_simulate(const float* d_h, awo_grid g, const uint32_t*
     a.muD = p->mu * D;
     a.N = p->traj_per_cell;
     a.max_steps = p->max_steps;
-    a.key0 = (uint32_t)(p->seed & 0xffffffffu);
-    a.key1 = (uint32_t)(p->seed >> 32);
+    a.cells_per_fetch = a.N >= SIM_FETCH_ITEMS ? 1u : (SIM_FETCH_ITEMS + a.N - 1u) / a.N;
+    uint32_t k0 = (uint32_t)(p->seed & 0xffffffffu), k1 = (uint32_t)(p->seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        a.rk0[r] = k0;
+        a.rk1[r] = k1;
+        k0 += 0x9E3779B9u;  // Weyl key schedule of Philox4x32
+        k1 += 0xBB67AE85u;
+    }
     a.count = d_count;
     a.maxe = d_maxe;
     a.ws = ws;
+    a.starts = reinterpret_cast<CellStart*>(static_cast<char*>(d_ws) + starts_offset());
 
     if (a.N > 0 && (n_cells_max > 0)) {
+        const unsigned pro_blocks = stream_blocks((int64_t)n_cells_max, 256);
+        k_sim_starts<<<pro_blocks, 256, 0, s>>>(a);
         unsigned blocks = (unsigned)(sm_count() * sim_blocks_per_sm());
         k_simulate<<<blocks, SIM_THREADS, 0, s>>>(a);
         awo_status st = launch_status();

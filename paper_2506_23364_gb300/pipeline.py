@@ -43,7 +43,7 @@ class Overlay:
         self.cells = torch.empty(n, dtype=torch.int32, device=d)
         self.n_rel = torch.zeros(1, dtype=torch.int32, device=d)
         self.ws_rel = _ws(awo_release_workspace_bytes(self.g), d)
-        self.ws_sim = _ws(awo_simulate_workspace_bytes(), d)
+        self.ws_sim = _ws(awo_simulate_workspace_bytes(n), d)
         self.count = torch.zeros((height, width), dtype=torch.int32, device=d)
         self.maxe = torch.zeros((height, width), dtype=torch.float32, device=d)
         self.vel = torch.empty((height, width), dtype=torch.float32, device=d)

@@ -49,7 +49,8 @@ def test_status_strings_and_version(L):
 
 
 def test_workspace_sizes(L):
-    assert awo.awo_simulate_workspace_bytes() >= 48
+    assert awo.awo_simulate_workspace_bytes(0) >= 48
+    assert awo.awo_simulate_workspace_bytes(1000) >= awo.awo_simulate_workspace_bytes(0) + 16000
     g = awo.grid(8192, 8192, 10.0)
     assert awo.awo_release_workspace_bytes(g) >= 2 * 4 * (8192 * 8192 // 4096)
     assert awo.awo_release_workspace_bytes(awo.grid(0, 5, 1.0)) == 0
