@@ -17,8 +17,8 @@
 //    the cell that start together).  Each loop iteration is then exactly one
 //    move and its visit -- direction from the footprint kept in registers,
 //    draw, step, footprint and energy at the new position, record -- written
-//    without data-dependent branches except the merged record, so a warp runs
-//    one instruction stream.
+//    without data-dependent branches (selects and predicated reductions), so
+//    a warp runs one instruction stream.
 //  * Visits go to the rasters as fire-and-forget reductions (RED.ADD on the
 //    count, RED.MAX on the bits of the non-negative energy); lanes of a warp
 //    that hit the same cell are merged first (__match_any_sync), which
@@ -71,7 +71,7 @@ struct SimArgs {
 };
 
 constexpr int SIM_THREADS = 256;
-constexpr uint32_t SIM_FETCH_ITEMS = 256;  // particles per global fetch, at least
+constexpr uint32_t SIM_FETCH_ITEMS = 1024;  // particles per global fetch, at least
 
 // Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64 products
 // of the even words and a word permutation that mixes in the round key.
@@ -205,7 +205,8 @@ __global__ void __launch_bounds__(SIM_THREADS) k_simulate(const __grid_constant_
 
     // lane state: position, its footprint and height, direction, energy,
     // recorded moves n (n == 0 only before the first move, when the footprint
-    // registers are not used)
+    // registers are not used).  A dead lane keeps a position inside the grid,
+    // so the loads it issues in the branch-free body stay in bounds.
     bool live = false;
     uint32_t cell = 0, j = 0, n = 0;
     float u = 0.f, v = 0.f, z = 0.f, dx = 0.f, dy = 0.f, e = 0.f;
@@ -215,79 +216,75 @@ __global__ void __launch_bounds__(SIM_THREADS) k_simulate(const __grid_constant_
     unsigned my_traj = 0, my_exit = 0, my_cap = 0, my_stop = 0, my_bad = 0;
 
     while (true) {
-        // ---- refill idle lanes: start particles at their release cell -------
-        unsigned idle = __ballot_sync(0xffffffffu, !live);
-        while (idle != 0u && !exhausted) {
+        // ---- refill idle lanes (one round per move) ------------------------
+        const unsigned idle = __ballot_sync(0xffffffffu, !live);
+        if (idle != 0u && !exhausted) {
             if (cur_ci >= end_ci) {
                 unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(&a.ws->next_cell, (unsigned long long)a.cells_per_fetch);
                 base = __shfl_sync(0xffffffffu, base, 0);
-                if (base >= n_cells) {
-                    exhausted = true;
-                    break;
-                }
-                cur_ci = (uint32_t)base;
+                exhausted = base >= n_cells;
+                cur_ci = (uint32_t)min(base, (unsigned long long)n_cells);
                 cur_j = 0;
                 end_ci = (uint32_t)min((unsigned long long)n_cells, base + a.cells_per_fetch);
             }
-            // particles left in the group (capped at 32)
-            unsigned long long left = (unsigned long long)(end_ci - cur_ci) * a.N - cur_j;
-            unsigned avail = left < 32ull ? (unsigned)left : 32u;
-            unsigned want = (unsigned)__popc(idle);
-            unsigned take = want < avail ? want : avail;
-            unsigned rank = (unsigned)__popc(idle & lane_lt);
-            if (((idle >> lane) & 1u) && rank < take) {
+            if (!exhausted) {
+                // particles left in the group (capped at 32)
+                const unsigned long long left = (unsigned long long)(end_ci - cur_ci) * a.N - cur_j;
+                const unsigned avail = left < 32ull ? (unsigned)left : 32u;
+                const unsigned want = (unsigned)__popc(idle);
+                const unsigned take = want < avail ? want : avail;
+                const unsigned rank = (unsigned)__popc(idle & lane_lt);
+                const bool mine = ((idle >> lane) & 1u) && rank < take;
                 uint32_t ci = cur_ci, jj = cur_j;
-                advance(ci, jj, rank, a.N);
-                const uint4 st = __ldg(reinterpret_cast<const uint4*>(a.starts) + ci);
-                if (st.x != ~0u) {
-                    cell = (st.x >> 16) * (uint32_t)a.W + (st.x & 0xffffu);
-                    j = jj;
-                    u = __int2float_rn((int)(st.x & 0xffffu));
-                    v = __int2float_rn((int)(st.x >> 16));
-                    z = __uint_as_float(st.y);
-                    dx = __uint_as_float(st.z);
-                    dy = __uint_as_float(st.w);
-                    n = 0;
-                    e = 0.f;
-                    if (a.max_steps == 0u) {
-                        ++my_cap;  // capped at the release visit
-                        ++my_traj;
-                    } else {
-                        live = true;
-                    }
-                } else {
-                    ++my_bad;  // release index outside the grid: skipped, reported
-                }
+                advance(ci, jj, rank < take ? rank : 0u, a.N);
+                uint4 st = make_uint4(~0u, 0u, 0u, 0u);
+                if (mine) st = __ldg(reinterpret_cast<const uint4*>(a.starts) + ci);
+                const bool ok = mine && st.x != ~0u;
+                my_bad += (mine && !ok) ? 1u : 0u;  // release index outside the grid: skipped, reported
+                const uint32_t sx = st.x & 0xffffu, sy = st.x >> 16;
+                cell = ok ? sy * (uint32_t)a.W + sx : cell;
+                j = ok ? jj : j;
+                u = ok ? __int2float_rn((int)sx) : u;
+                v = ok ? __int2float_rn((int)sy) : v;
+                z = ok ? __uint_as_float(st.y) : z;
+                dx = ok ? __uint_as_float(st.z) : dx;
+                dy = ok ? __uint_as_float(st.w) : dy;
+                n = ok ? 0u : n;
+                e = ok ? 0.0f : e;
+                const bool cap0 = ok && a.max_steps == 0u;  // capped at the release visit
+                my_cap += cap0 ? 1u : 0u;
+                my_traj += cap0 ? 1u : 0u;
+                live = live || (ok && !cap0);
+                advance(cur_ci, cur_j, take, a.N);
             }
-            advance(cur_ci, cur_j, take, a.N);
-            idle = __ballot_sync(0xffffffffu, !live);
         }
         const unsigned active = __ballot_sync(0xffffffffu, live);
-        if (active == 0u) break;
-        if (!live) continue;
+        if (active == 0u) {
+            if (exhausted) break;
+            continue;
+        }
 
         // ---- one move: direction at p, draw, step, energy at p' ------------
+        // (every lane computes; only live lanes record and update)
         const float ox = __fsub_rn(1.0f, fx), oy = __fsub_rn(1.0f, fy);
         // steepest descent of the bilinear patch at p; the previous direction
-        // when flat (d = 0 before the first move)
+        // when flat.  Before the first move d holds d_0 = g(p_0) from the
+        // start record, which is also the steepest descent at p_0.
         const float ga = __fadd_rn(__fmul_rn(__fsub_rn(h10, h00), oy), __fmul_rn(__fsub_rn(h11, h01), fy));
         const float gb = __fadd_rn(__fmul_rn(__fsub_rn(h01, h00), ox), __fmul_rn(__fsub_rn(h11, h10), fx));
         const float gn2 = __fadd_rn(__fmul_rn(ga, ga), __fmul_rn(gb, gb));
         const float ginv = __frcp_rn(__fsqrt_rn(gn2));
-        // before the first move d holds d_0 = g(p_0) from the start record,
-        // which is also the steepest descent at p_0
         const bool keep = (gn2 == 0.0f) || (n == 0u);
         const float gx = keep ? dx : __fmul_rn(-ga, ginv);
         const float gy = keep ? dy : __fmul_rn(-gb, ginv);
-        const float px = dx, py = dy;
 
         const uint4 w = philox4x32_10(make_uint4(cell, j, n >> 1, 0u), a.rk0, a.rk1);
         const bool odd = (n & 1u) != 0u;
         const float xix = uniform_pm1(odd ? w.z : w.x);
         const float xiy = uniform_pm1(odd ? w.w : w.y);
-        const float rx = __fadd_rn(__fadd_rn(__fmul_rn(a.P, px), __fmul_rn(a.oneP, gx)), __fmul_rn(a.R, xix));
-        const float ry = __fadd_rn(__fadd_rn(__fmul_rn(a.P, py), __fmul_rn(a.oneP, gy)), __fmul_rn(a.R, xiy));
+        const float rx = __fadd_rn(__fadd_rn(__fmul_rn(a.P, dx), __fmul_rn(a.oneP, gx)), __fmul_rn(a.R, xix));
+        const float ry = __fadd_rn(__fadd_rn(__fmul_rn(a.P, dy), __fmul_rn(a.oneP, gy)), __fmul_rn(a.R, xiy));
         const float r2 = __fadd_rn(__fmul_rn(rx, rx), __fmul_rn(ry, ry));
         const float rinv = __frcp_rn(__fsqrt_rn(r2));
         const bool zero_dir = (r2 == 0.0f);
@@ -300,39 +297,41 @@ __global__ void __launch_bounds__(SIM_THREADS) k_simulate(const __grid_constant_
         const Foot f = gather(a.h, a.W, a.H, inside ? u1 : u, inside ? v1 : v);
         const float z1 = bilinear(f, __fsub_rn(1.0f, f.fx), __fsub_rn(1.0f, f.fy));
         const float e1 = __fsub_rn(__fadd_rn(__fsub_rn(e, __fmul_rn(a.kD, e)), __fsub_rn(z, z1)), a.muD);
-        const bool moved = inside && e1 > 0.0f;
+        const bool moved = live && inside && e1 > 0.0f;
 
-        const unsigned rec = __ballot_sync(active, moved);
-        if (moved) {
-            const uint32_t vidx = (uint32_t)(f.j0 + (f.fy >= 0.5f ? 1 : 0)) * (uint32_t)a.W +
-                                  (uint32_t)(f.i0 + (f.fx >= 0.5f ? 1 : 0));
-            record(a.count, a.maxe, rec, vidx, e1);
-            u = u1;
-            v = v1;
-            z = z1;
-            e = e1;
-            dx = ndx;
-            dy = ndy;
-            fx = f.fx;
-            fy = f.fy;
-            h00 = f.h00;
-            h10 = f.h10;
-            h01 = f.h01;
-            h11 = f.h11;
-            ++n;
-            ++my_steps;
-            if (n == a.max_steps) {
-                live = false;
-                ++my_cap;
-            }
-        } else {
-            live = false;
-            if (inside || zero_dir)
-                ++my_stop;  // energy exhausted (or no direction): not recorded
-            else
-                ++my_exit;
+        // merged visit over the lanes that moved; the others share a key no
+        // cell has and issue nothing
+        const uint32_t vidx = (uint32_t)(f.j0 + (f.fy >= 0.5f ? 1 : 0)) * (uint32_t)a.W +
+                              (uint32_t)(f.i0 + (f.fx >= 0.5f ? 1 : 0));
+        const uint32_t key = moved ? vidx : 0xffffffffu;
+        const unsigned grp = __match_any_sync(0xffffffffu, key);
+        const unsigned emax = __reduce_max_sync(grp, moved ? __float_as_uint(e1) : 0u);
+        if (moved && (unsigned)lane == (unsigned)(__ffs(grp) - 1)) {
+            atomicAdd(a.count + vidx, (unsigned)__popc(grp));
+            atomicMax(reinterpret_cast<unsigned*>(a.maxe) + vidx, emax);
         }
-        if (!live) ++my_traj;
+
+        u = moved ? u1 : u;
+        v = moved ? v1 : v;
+        z = moved ? z1 : z;
+        e = moved ? e1 : e;
+        dx = moved ? ndx : dx;
+        dy = moved ? ndy : dy;
+        fx = moved ? f.fx : fx;
+        fy = moved ? f.fy : fy;
+        h00 = moved ? f.h00 : h00;
+        h10 = moved ? f.h10 : h10;
+        h01 = moved ? f.h01 : h01;
+        h11 = moved ? f.h11 : h11;
+        n += moved ? 1u : 0u;
+        my_steps += moved ? 1u : 0u;
+        const bool capped = moved && n == a.max_steps;
+        const bool ended = live && (!moved || capped);
+        my_cap += capped ? 1u : 0u;
+        my_stop += (live && !moved && (inside || zero_dir)) ? 1u : 0u;  // energy exhausted or no direction
+        my_exit += (live && !inside && !zero_dir) ? 1u : 0u;
+        my_traj += ended ? 1u : 0u;
+        live = live && !ended;
     }
 
     // ---- statistics -----------------------------------------------------
