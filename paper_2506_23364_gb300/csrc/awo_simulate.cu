@@ -20,10 +20,10 @@
 //    without data-dependent branches (selects and predicated reductions), so
 //    a warp runs one instruction stream.
 //  * Visits go to the rasters as fire-and-forget reductions (RED.ADD on the
-//    count, RED.MAX on the bits of the non-negative energy); lanes of a warp
-//    that hit the same cell are merged first (__match_any_sync), which
-//    removes nearly all reductions while the particles of a cell still move
-//    together.
+//    count, RED.MAX on the bits of the non-negative energy), one pair per
+//    lane: measured on GB300, merging the lanes of a warp that hit the same
+//    cell (__match_any_sync + __reduce_max_sync) costs more issue slots than
+//    the L2 spends on the duplicate reductions.
 //  * Philox4x32-10 round keys are computed once on the host and read from the
 //    kernel's parameter bank.
 //  * Arithmetic is FP32 with explicit round-to-nearest intrinsics: no fused
@@ -70,7 +70,7 @@ struct SimArgs {
     CellStart* starts;     // one per release-list entry
 };
 
-constexpr int SIM_THREADS = 256;
+constexpr int SIM_THREADS = 128;
 constexpr uint32_t SIM_FETCH_ITEMS = 1024;  // particles per global fetch, at least
 
 // Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64 products
@@ -105,13 +105,14 @@ __device__ __forceinline__ Foot gather(const float* __restrict__ h, int W, int H
     f.j0 = __float2int_rd(v);
     f.fx = __fsub_rn(u, __int2float_rn(f.i0));
     f.fy = __fsub_rn(v, __int2float_rn(f.j0));
+    // 32-bit offsets: W * H < 2^31
     const int di = f.i0 + 1 < W ? 1 : 0;
-    const size_t dj = f.j0 + 1 < H ? (size_t)W : 0;
-    const float* p = h + (size_t)f.j0 * (size_t)W + f.i0;
-    f.h00 = __ldg(p);
-    f.h10 = __ldg(p + di);
-    f.h01 = __ldg(p + dj);
-    f.h11 = __ldg(p + dj + di);
+    const int dj = f.j0 + 1 < H ? W : 0;
+    const int o = f.j0 * W + f.i0;
+    f.h00 = __ldg(h + o);
+    f.h10 = __ldg(h + (o + di));
+    f.h01 = __ldg(h + (o + dj));
+    f.h11 = __ldg(h + (o + dj + di));
     return f;
 }
 
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(SIM_THREADS) k_simulate(const __grid_constant_
     float fx = 0.f, fy = 0.f, h00 = 0.f, h10 = 0.f, h01 = 0.f, h11 = 0.f;
 
     unsigned long long my_steps = 0;
-    unsigned my_traj = 0, my_exit = 0, my_cap = 0, my_stop = 0, my_bad = 0;
+    unsigned my_traj = 0, my_exit = 0, my_cap = 0, my_bad = 0;
 
     while (true) {
         // ---- refill idle lanes (one round per move) ------------------------
@@ -299,16 +300,14 @@ __global__ void __launch_bounds__(SIM_THREADS) k_simulate(const __grid_constant_
         const float e1 = __fsub_rn(__fadd_rn(__fsub_rn(e, __fmul_rn(a.kD, e)), __fsub_rn(z, z1)), a.muD);
         const bool moved = live && inside && e1 > 0.0f;
 
-        // merged visit over the lanes that moved; the others share a key no
-        // cell has and issue nothing
+        // the visit: two fire-and-forget reductions per lane that moved (the
+        // L2 absorbs lanes of a warp that hit the same cell more cheaply than
+        // merging them in the warp first)
         const uint32_t vidx = (uint32_t)(f.j0 + (f.fy >= 0.5f ? 1 : 0)) * (uint32_t)a.W +
                               (uint32_t)(f.i0 + (f.fx >= 0.5f ? 1 : 0));
-        const uint32_t key = moved ? vidx : 0xffffffffu;
-        const unsigned grp = __match_any_sync(0xffffffffu, key);
-        const unsigned emax = __reduce_max_sync(grp, moved ? __float_as_uint(e1) : 0u);
-        if (moved && (unsigned)lane == (unsigned)(__ffs(grp) - 1)) {
-            atomicAdd(a.count + vidx, (unsigned)__popc(grp));
-            atomicMax(reinterpret_cast<unsigned*>(a.maxe) + vidx, emax);
+        if (moved) {
+            atomicAdd(a.count + vidx, 1u);
+            atomicMax(reinterpret_cast<unsigned*>(a.maxe) + vidx, __float_as_uint(e1));
         }
 
         u = moved ? u1 : u;
@@ -328,8 +327,7 @@ __global__ void __launch_bounds__(SIM_THREADS) k_simulate(const __grid_constant_
         const bool capped = moved && n == a.max_steps;
         const bool ended = live && (!moved || capped);
         my_cap += capped ? 1u : 0u;
-        my_stop += (live && !moved && (inside || zero_dir)) ? 1u : 0u;  // energy exhausted or no direction
-        my_exit += (live && !inside && !zero_dir) ? 1u : 0u;
+        my_exit += (live && !inside && !zero_dir) ? 1u : 0u;  // the other ends are stops
         my_traj += ended ? 1u : 0u;
         live = live && !ended;
     }
@@ -341,7 +339,6 @@ __global__ void __launch_bounds__(SIM_THREADS) k_simulate(const __grid_constant_
         my_traj += __shfl_xor_sync(0xffffffffu, my_traj, o);
         my_exit += __shfl_xor_sync(0xffffffffu, my_exit, o);
         my_cap += __shfl_xor_sync(0xffffffffu, my_cap, o);
-        my_stop += __shfl_xor_sync(0xffffffffu, my_stop, o);
         my_bad += __shfl_xor_sync(0xffffffffu, my_bad, o);
     }
     if (lane == 0) {
@@ -349,7 +346,7 @@ __global__ void __launch_bounds__(SIM_THREADS) k_simulate(const __grid_constant_
         atomicAdd(&a.ws->n_traj, (unsigned long long)my_traj);
         atomicAdd(&a.ws->n_exited, (unsigned long long)my_exit);
         atomicAdd(&a.ws->n_capped, (unsigned long long)my_cap);
-        atomicAdd(&a.ws->n_stopped, (unsigned long long)my_stop);
+        atomicAdd(&a.ws->n_stopped, (unsigned long long)(my_traj - my_exit - my_cap));
         if (my_bad) atomicAdd(&a.ws->n_rejected, (unsigned long long)my_bad);
     }
 }
