@@ -196,6 +196,70 @@ awo_status awo_simulate(const float* d_h, awo_grid g, const uint32_t* d_cells,
                         awo_sim_stats* d_stats, void* d_ws, size_t ws_bytes, void* stream);
 
 /*
+ * c (batched). Particle trajectories for many regions in one persistent
+ * launch (the paper's workflow re-run for many regions and parameter sets;
+ * Sec. 5.2 lets the user change the parameters interactively).  Every request
+ * gets exactly the rasters and statistics that awo_simulate would give it
+ * alone (same formulas, same Philox streams; reductions are
+ * order-independent), whatever the tuning.
+ *  - reqs: HOST array of n_req (1..AWO_BATCH_MAX) requests; each one as in
+ *    awo_simulate (its own DEM, grid, release list with optional device-side
+ *    count, parameters incl. seed and AWO_SIM_CLEAR_OUTPUTS, and rasters).
+ *    Rasters of different requests must not overlap.  The sum of n_cells_max
+ *    over the requests must be < 2^31.
+ *  - tuning: NULL for the default, or a configuration from awo_tune_batched.
+ *  - d_stats: device array of n_req awo_sim_stats, overwritten (nullable).
+ *  - Workspace: awo_simulate_batched_workspace_bytes(reqs, n_req) bytes,
+ *    16-byte aligned, contents undefined on entry and exit.
+ * The request table travels in the kernel's parameter block: the call makes
+ * no host-to-device copy and no allocation.
+ */
+#define AWO_BATCH_MAX 128
+
+typedef struct {
+    const float* d_h;
+    awo_grid grid;
+    const uint32_t* d_cells;
+    const uint32_t* d_n_cells;   /* nullable */
+    uint32_t n_cells_max;
+    uint32_t reserved;
+    awo_sim_params params;
+    uint32_t* d_count;
+    float* d_maxe;
+} awo_sim_request;
+
+/* Launch shape of the batched particle kernel (the autotuner's search space).
+ *   threads_per_block: 64, 128 or 256 (0 = 128)
+ *   group_particles:   particles a warp takes per fetch, 32 .. 65536 (0 = 1024)
+ *   refill: AWO_REFILL_LANE -- a lane starts the next particle as soon as its
+ *           particle ends (trajectory per thread, continuously refilled);
+ *           AWO_REFILL_WARP -- a warp starts 32 particles together and takes
+ *           the next 32 only when all have ended (trajectories per warp, in
+ *           lock-step batches). */
+#define AWO_REFILL_LANE 0
+#define AWO_REFILL_WARP 1
+typedef struct {
+    int32_t threads_per_block;
+    int32_t group_particles;
+    int32_t refill;
+    int32_t reserved;
+} awo_tuning;
+
+size_t awo_simulate_batched_workspace_bytes(const awo_sim_request* reqs, int32_t n_req);
+awo_status awo_simulate_batched(const awo_sim_request* reqs, int32_t n_req, const awo_tuning* tuning,
+                                awo_sim_stats* d_stats, void* d_ws, size_t ws_bytes, void* stream);
+
+/*
+ * Autotuner: times every launch shape of the search space (threads per block
+ * x group size x refill policy) on this batch with CUDA events and returns
+ * the fastest in *best (and its time in *best_ms, nullable).  Each timed run
+ * clears the requests' rasters first, so on return they hold the batch's
+ * result.  Synchronises `stream`; not for use during stream capture.
+ */
+awo_status awo_tune_batched(const awo_sim_request* reqs, int32_t n_req, void* d_ws, size_t ws_bytes,
+                            void* stream, awo_tuning* best, float* best_ms);
+
+/*
  * c'. Velocity indicator (Fig. 4: the colour encodes Z^delta_max, read as a
  * velocity): d_vel[i] = sqrt((2*gravity) * d_maxe[i]).  Exact.
  * d_vel may alias d_maxe.

@@ -56,6 +56,25 @@ class SimParams(ctypes.Structure):
                    seed, flags, 0)
 
 
+class SimRequest(ctypes.Structure):
+    """awo_sim_request: one region of a batched particle launch."""
+    _fields_ = [("d_h", ctypes.c_void_p), ("grid", Grid), ("d_cells", ctypes.c_void_p),
+                ("d_n_cells", ctypes.c_void_p), ("n_cells_max", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("params", SimParams), ("d_count", ctypes.c_void_p), ("d_maxe", ctypes.c_void_p)]
+
+
+class Tuning(ctypes.Structure):
+    """awo_tuning: launch shape of the batched particle kernel."""
+    _fields_ = [("threads_per_block", ctypes.c_int32), ("group_particles", ctypes.c_int32),
+                ("refill", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {"threads_per_block": int(self.threads_per_block), "group_particles": int(self.group_particles),
+                "refill": "warp" if self.refill == REFILL_WARP else "lane"}
+
+
+REFILL_LANE, REFILL_WARP = 0, 1
+BATCH_MAX = 128
 STATS_FIELDS = ("total_steps", "n_traj", "n_exited", "n_capped", "n_stopped", "n_rejected")
 
 _lib = None
@@ -84,6 +103,9 @@ def lib() -> ctypes.CDLL:
         "awo_simulate": (st, [vp, Grid, vp, vp, u32, ctypes.POINTER(SimParams), vp, vp, vp, vp, sz, vp]),
         "awo_finalize": (st, [vp, Grid, f32, vp, vp]),
         "awo_overlay_lod": (st, [vp, vp, Grid, i32, vp, vp, vp]),
+        "awo_simulate_batched_workspace_bytes": (sz, [vp, i32]),
+        "awo_simulate_batched": (st, [vp, i32, vp, vp, vp, sz, vp]),
+        "awo_tune_batched": (st, [vp, i32, vp, sz, vp, vp, vp]),
         "awo_probe_l2_gather": (st, [vp, u32, u32, vp, vp]),
         "awo_probe_l2_red": (st, [vp, u32, u32, vp]),
         "awo_probe_threads": (ctypes.c_uint64, []),
@@ -209,6 +231,58 @@ def awo_simulate(h: torch.Tensor, g: Grid, cells: torch.Tensor | None, n_cells_d
                               _dev(ws, torch.uint8, None, "ws"), ws.numel(), _stream(stream)), "awo_simulate")
 
 
+def sim_request(h: torch.Tensor, g: Grid, cells: torch.Tensor | None, n_cells_dev: torch.Tensor | None,
+                n_cells_max: int, params: SimParams, count: torch.Tensor, maxe: torch.Tensor) -> SimRequest:
+    """Checks the tensors of one region and packs them as an awo_sim_request."""
+    c = g.cells
+    if count.dtype not in (torch.int32, torch.uint32):
+        raise TypeError("count must be int32 or uint32")
+    cp = None
+    if cells is not None:
+        if cells.dtype not in (torch.int32, torch.uint32):
+            raise TypeError("cells must be int32 or uint32")
+        cp = _dev(cells, cells.dtype, n_cells_max, "cells")
+    nd = _dev(n_cells_dev, n_cells_dev.dtype, 1, "n_cells_dev") if n_cells_dev is not None else None
+    return SimRequest(_dev(h, torch.float32, c, "h"), g, cp, nd, int(n_cells_max), 0, params,
+                      _dev(count, count.dtype, c, "count"), _dev(maxe, torch.float32, c, "maxe"))
+
+
+def _req_array(reqs):
+    if isinstance(reqs, ctypes.Array):
+        return reqs
+    arr = (SimRequest * len(reqs))()
+    for i, r in enumerate(reqs):
+        arr[i] = r
+    return arr
+
+
+def awo_simulate_batched_workspace_bytes(reqs) -> int:
+    arr = _req_array(reqs)
+    n = int(lib().awo_simulate_batched_workspace_bytes(arr, len(arr)))
+    if n == 0:
+        raise AwoError(AWO_EINVAL, "awo_simulate_batched_workspace_bytes")
+    return n
+
+
+def awo_simulate_batched(reqs, ws: torch.Tensor, tuning: Tuning | None = None, stats: torch.Tensor | None = None,
+                         stream=None):
+    """One persistent launch over all regions; stats: int64 [n_req, 6] on the device."""
+    arr = _req_array(reqs)
+    sp = _dev(stats, torch.int64, 6 * len(arr), "stats") if stats is not None else None
+    _check(lib().awo_simulate_batched(arr, len(arr), ctypes.byref(tuning) if tuning is not None else None, sp,
+                                      _dev(ws, torch.uint8, None, "ws"), ws.numel(), _stream(stream)),
+           "awo_simulate_batched")
+
+
+def awo_tune_batched(reqs, ws: torch.Tensor, stream=None) -> tuple[Tuning, float]:
+    arr = _req_array(reqs)
+    best = Tuning()
+    ms = ctypes.c_float(0.0)
+    _check(lib().awo_tune_batched(arr, len(arr), _dev(ws, torch.uint8, None, "ws"), ws.numel(), _stream(stream),
+                                  ctypes.byref(best), ctypes.byref(ms)), "awo_tune_batched")
+    return best, float(ms.value)
+
+
 def awo_finalize(maxe: torch.Tensor, g: Grid, gravity: float, vel: torch.Tensor, stream=None):
     _check(lib().awo_finalize(_dev(maxe, torch.float32, g.cells, "maxe"), g, gravity,
                               _dev(vel, torch.float32, g.cells, "vel"), _stream(stream)), "awo_finalize")
@@ -266,3 +340,4 @@ def stats_dict(stats: torch.Tensor) -> dict:
 
 
 from .pipeline import Overlay  # noqa: E402  (re-export)
+from .batch import Batch  # noqa: E402  (re-export)

@@ -42,4 +42,21 @@ inline unsigned stream_blocks(int64_t work_items, int threads, int per_sm = 8)
     return (unsigned)want;
 }
 
+// Validates particle parameters for a grid of cell size cs (see awo.h).
+inline bool sim_params_ok(const awo_sim_params* p, float cs)
+{
+    if (!p) return false;
+    if (!(p->persistence >= 0.0f && p->persistence <= 1.0f)) return false;
+    if (!(p->randomness >= 0.0f) || !(p->randomness < 3.0e38f)) return false;
+    if (!(p->mu >= 0.0f) || !(p->mu < 3.0e38f)) return false;
+    if (!(p->drag_k >= 0.0f) || !(p->drag_k < 3.0e38f)) return false;
+    if (!(p->step_scale > 0.0f) || !(p->step_scale <= 1.0f)) return false;
+    if (!(p->gravity > 0.0f) || !(p->gravity < 3.0e38f)) return false;
+    const float D = p->step_scale * cs;
+    const float kD = p->drag_k * D;
+    if (!(kD < 1.0f)) return false;
+    if ((p->flags & ~AWO_SIM_CLEAR_OUTPUTS) != 0u) return false;
+    return true;
+}
+
 }  // namespace awo

@@ -88,3 +88,25 @@ def test_bad_arguments_rejected_on_host(L):
     assert L.awo_overlay_lod(fake, fake, G, 0, arr, arr, None) == awo.AWO_EINVAL
     assert L.awo_overlay_lod(fake, fake, G, 17, arr, arr, None) == awo.AWO_EINVAL
     assert L.awo_overlay_lod(fake, fake, G, 2, None, None, None) == awo.AWO_EINVAL
+
+
+def test_batched_structs_and_host_validation(L):
+    assert ctypes.sizeof(awo.SimRequest) == 112 and awo.SimRequest.params.offset == 48
+    assert ctypes.sizeof(awo.Tuning) == 16
+    G = awo.grid(16, 16, 10.0)
+    fake = 256
+    r = awo.SimRequest(fake, G, fake, None, 4, 0, awo.SimParams.make(), fake, fake)
+    arr = (awo.SimRequest * 1)(r)
+    ws_need = L.awo_simulate_batched_workspace_bytes(arr, 1)
+    assert ws_need >= 4 * 16
+    assert L.awo_simulate_batched_workspace_bytes(arr, 0) == 0
+    assert L.awo_simulate_batched(arr, 0, None, None, fake, ws_need, None) == awo.AWO_EINVAL
+    assert L.awo_simulate_batched(arr, 129, None, None, fake, ws_need, None) == awo.AWO_EINVAL
+    assert L.awo_simulate_batched(arr, 1, None, None, fake, ws_need - 1, None) == awo.AWO_ENOMEM
+    for t in (awo.Tuning(100, 0, 0, 0), awo.Tuning(128, 16, 0, 0), awo.Tuning(128, 1024, 2, 0)):
+        assert L.awo_simulate_batched(arr, 1, ctypes.byref(t), None, fake, ws_need, None) == awo.AWO_EINVAL
+    bad = awo.SimRequest(fake, G, fake, None, 4, 0, awo.SimParams.make(persistence=3.0), fake, fake)
+    arr2 = (awo.SimRequest * 2)(r, bad)
+    assert L.awo_simulate_batched(arr2, 2, None, None, fake, 1 << 20, None) == awo.AWO_EINVAL
+    best = awo.Tuning()
+    assert L.awo_tune_batched(arr, 0, fake, ws_need, None, ctypes.byref(best), None) == awo.AWO_EINVAL
