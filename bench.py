@@ -27,6 +27,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -60,7 +62,9 @@ def _args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["awo", "reference"], default="awo")
-    ap.add_argument("--workload", choices=["large", "mid", "tiny"], default="large")
+    ap.add_argument("--workload", choices=["large", "mid", "tiny", "batched", "served"], default="large")
+    ap.add_argument("--batch-n", type=int, default=64, help="regions of the batched/served workload")
+    ap.add_argument("--rate", type=float, default=200.0, help="Poisson arrival rate of the served workload (1/s)")
     ap.add_argument("--crop", type=int, default=0, help="use the top-left N x N crop of the workload's DEM")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -396,6 +400,113 @@ def run_awo(args, R: Ranks):
         print(json.dumps(line), flush=True)
 
 
+def _region_params(awo, r):
+    return awo.SimParams.make(**r.params)
+
+
+def run_batched(args, R: Ranks):
+    """Many regions: each region run alone in sequence (the plain form) against
+    one batched launch per pass (tuned once, replayed from a CUDA graph)."""
+    import torch
+
+    import paper_2506_23364_gb300 as awo
+    from paper_2506_23364_gb300 import inputs
+
+    reqs = inputs.batched_requests(args.batch_n)
+    params = [_region_params(awo, r) for r in reqs]
+    cs = reqs[0].cell_size
+    ovs = []
+    for r in reqs:
+        H, W = r.dem_u16.shape
+        ov = awo.Overlay(W, H, cs, quantised=True, levels=1, device=R.device, want_normals=False, want_mask=False)
+        ov.load_dem(r.dem_u16)
+        ovs.append(ov)
+
+    def plain():
+        for ov, r, p in zip(ovs, reqs, params):
+            ov.run(*r.release_deg, p)
+
+    def timed(fn, k):
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(k):
+            fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / k
+
+    ms_plain = timed(plain, args.steps)
+    steps_plain = sum(ov.stats_dict()["total_steps"] for ov in ovs)
+    del ovs
+    torch.cuda.empty_cache()
+    batch = awo.Batch([r.dem_u16 for r in reqs], cs, params, [r.release_deg for r in reqs], quantised=True,
+                      device=R.device)
+    tuning, tune_ms = batch.tune()
+    batch.capture()
+    clocks = ClockSampler(R.local)
+    clocks.start()
+    ms_batch = timed(batch.replay, args.steps)
+    clk = clocks.stop()
+    st = batch.stats_list()
+    steps_batch = sum(x["total_steps"] for x in st)
+    assert steps_batch == steps_plain, "batched and plain runs must make the same moves"
+    cells = sum(r.dem_u16.size for r in reqs)
+    line = {"metric": "aggregate trajectory-steps/s, batched regions", "value": steps_batch / (ms_batch / 1e3),
+            "unit": UNIT, "n_gpus": R.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic (seeded fBm regions, uint16 dm)",
+            "config": {"workload": f"batched-{len(reqs)}-regions-512..4096", "cells": cells,
+                       "particles": sum(x["n_traj"] for x in st), "form": "one batched launch per pass, CUDA graph",
+                       "tuning": tuning.as_dict(), "tune_best_ms": tune_ms},
+            "plain": {"value": steps_plain / (ms_plain / 1e3), "ms_per_pass": ms_plain,
+                      "form": "each region alone, in sequence, same stream"},
+            "speedup_vs_plain": ms_plain / ms_batch, "clocks": clk}
+    if R.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_served(args, R: Ranks):
+    """Poisson arrivals of the batched workload's regions into the serving loop."""
+    import torch
+
+    from paper_2506_23364_gb300 import inputs
+    from paper_2506_23364_gb300.serve import OverlayRequest, OverlayServer, latency_summary
+
+    regs = inputs.batched_requests(args.batch_n)
+    mk = lambda r: OverlayRequest(r.dem_u16, r.cell_size, r.release_deg, dict(r.params))
+    srv = OverlayServer(budget_bytes=96 << 30, n_slots=4, max_batch=16, device=R.device)
+    for f in [srv.submit(mk(r)) for r in regs[:4]]:  # warm-up (library load, occupancy queries, allocator)
+        f.result()
+    arrivals = inputs.poisson_arrivals(len(regs), args.rate, seed=1)
+    clocks = ClockSampler(R.local)
+    clocks.start()
+    t0 = time.perf_counter()
+    futs = []
+    for r, at in zip(regs, arrivals):
+        dt = t0 + at - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        futs.append(srv.submit(mk(r)))
+    res = [f.result() for f in futs]
+    t_end = max(x.t_done for x in res)
+    clk = clocks.stop()
+    srv.shutdown()
+    ok = [x for x in res if x.status == "ok"]
+    steps = sum(x.stats["total_steps"] for x in ok)
+    lat = latency_summary(res)
+    line = {"metric": "served overlays: p50/p99 latency and aggregate trajectory-steps/s",
+            "value": steps / (t_end - t0), "unit": UNIT, "n_gpus": R.world, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic (seeded fBm regions, uint16 dm)",
+            "config": {"workload": f"served-{len(regs)}-regions-512..4096", "arrivals": f"Poisson {args.rate}/s",
+                       "slots": 4, "max_batch": 16, "budget_gib": 96},
+            "latency_ms": lat, "ok": len(ok), "mean_batch": float(np.mean([x.batch_size for x in ok])),
+            "wall_s": t_end - t0, "peak_budget_gib": srv.sched.peak_in_use / 2 ** 30, "clocks": clk}
+    if R.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args, R: Ranks):
     """The CPU oracle on the host cores: each step a bounded random sample of
     the workload's release cells (all particles of each)."""
@@ -446,6 +557,10 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, R)
+        elif args.workload == "batched":
+            run_batched(args, R)
+        elif args.workload == "served":
+            run_served(args, R)
         else:
             run_awo(args, R)
     finally:

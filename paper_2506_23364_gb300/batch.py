@@ -19,23 +19,32 @@ from . import (SimParams, SimRequest, Tuning, awo_simulate_batched, awo_simulate
 from .pipeline import SIM_CLEAR_OUTPUTS, Overlay
 
 
+def _per_region(x, n):
+    return list(x) if isinstance(x, (list, tuple)) else [x] * n
+
+
 class Batch:
-    def __init__(self, dems: list, cell_size: float, params: list[SimParams], release_deg: list[tuple[float, float]],
-                 *, quantised: bool, levels: int = 1, decode_scale: float = 0.1, device="cuda"):
+    """Regions may differ in size, cell size, DEM storage (uint16 decimetres or
+    float32 metres), mipmap depth and decode scale: pass a list for any of
+    these, or one value for all."""
+
+    def __init__(self, dems: list, cell_size, params: list[SimParams], release_deg: list[tuple[float, float]],
+                 *, quantised, levels=1, decode_scale=0.1, device="cuda", load: bool = True):
         if not (len(dems) == len(params) == len(release_deg)):
             raise ValueError("dems, params and release ranges must have the same length")
         self.n = len(dems)
-        self.decode_scale = decode_scale
+        self.decode_scale = _per_region(decode_scale, self.n)
         self.release_deg = list(release_deg)
         self.params = [SimParams.from_buffer_copy(p) for p in params]
         for p in self.params:
             p.flags |= SIM_CLEAR_OUTPUTS
         self.ovs = []
-        for dem in dems:
+        for dem, cs, qz, lv in zip(dems, _per_region(cell_size, self.n), _per_region(quantised, self.n),
+                                   _per_region(levels, self.n)):
             H, W = dem.shape
-            ov = Overlay(W, H, cell_size, quantised=quantised, levels=levels, device=device, want_normals=False,
-                         want_mask=False)
-            ov.load_dem(dem)
+            ov = Overlay(W, H, cs, quantised=qz, levels=lv, device=device, want_normals=False, want_mask=False)
+            if load:
+                ov.load_dem(dem)
             self.ovs.append(ov)
         self.reqs = (SimRequest * self.n)()
         for i, ov in enumerate(self.ovs):
@@ -48,8 +57,8 @@ class Batch:
         self.graph: torch.cuda.CUDAGraph | None = None
 
     def terrain(self, stream=None):
-        for ov, (lo, hi) in zip(self.ovs, self.release_deg):
-            ov.terrain(lo, hi, self.decode_scale, stream)
+        for ov, (lo, hi), sc in zip(self.ovs, self.release_deg, self.decode_scale):
+            ov.terrain(lo, hi, sc, stream)
 
     def simulate(self, stream=None):
         awo_simulate_batched(self.reqs, self.ws, self.tuning, self.stats, stream)

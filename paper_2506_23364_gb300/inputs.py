@@ -208,3 +208,50 @@ def crop(w: Workload, n: int) -> Workload:
     if w.dem_f32 is not None:
         out.dem_f32 = np.ascontiguousarray(w.dem_f32[:n, :n])
     return out
+
+
+# ----------------------------------------------------------------------------
+# Many regions (batched and served forms)
+# ----------------------------------------------------------------------------
+@dataclass
+class RegionRequest:
+    """One region of the batched/served workload."""
+    dem_u16: np.ndarray
+    cell_size: float
+    release_deg: tuple[float, float]
+    params: dict  # keyword arguments of SimParams.make
+
+
+def batched_requests(n: int = 64, seed: int = 0, sizes: tuple[int, int] = (512, 4096),
+                     workers: int = 8) -> list[RegionRequest]:
+    """Regions of side drawn uniformly from multiples of 64 in [512, 4096];
+    fBm (H = 0.8, seed 100 + i) with relief 3000 m * (side / 2048)^0.8, so
+    that every side has the slope statistics of the 2048^2 workload (fBm
+    increments grow as L^H) and its release range [43.1, 45] degrees selects
+    about 5% of the cells; mu = tan 25 deg and drag k = 1e-3 / m each scaled
+    by exp(U(ln 0.5, ln 1.5)); 32..256 particles per cell; cap 4000; Philox
+    seed i."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    rng = np.random.default_rng(seed)
+    lo, hi = sizes
+    sides = rng.integers(lo // 64, hi // 64 + 1, size=n) * 64
+    mus = float(np.tan(np.deg2rad(25.0))) * np.exp(rng.uniform(np.log(0.5), np.log(1.5), size=n))
+    ks = 1e-3 * np.exp(rng.uniform(np.log(0.5), np.log(1.5), size=n))
+    Ns = rng.integers(32, 257, size=n)
+
+    def one(i):
+        side = int(sides[i])
+        z = fbm(side, 0.8, seed=100 + i, relief=3000.0 * (side / 2048.0) ** 0.8)
+        return RegionRequest(quantise_dm(z), CELL_SIZE_M, MID_RELEASE_DEG,
+                             dict(mu=float(mus[i]), drag_k=float(ks[i]), traj_per_cell=int(Ns[i]),
+                                  max_steps=4000, seed=i))
+
+    with ThreadPoolExecutor(max(1, workers)) as ex:
+        return list(ex.map(one, range(n)))
+
+
+def poisson_arrivals(n: int, rate_per_s: float, seed: int = 0) -> np.ndarray:
+    """Arrival times (s) of a Poisson process of the given rate."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
