@@ -220,6 +220,77 @@ def trace(h: np.ndarray, cs: float, cell: int, j: int, params: SimParams,
             "end": END_NAMES[end.value]}
 
 
+SOFT_TAU = 1.0  # metres of energy-line height per e-fold of survival
+
+
+def soft_forward(h: np.ndarray, cs: float, cells: np.ndarray, weights: np.ndarray, params: SimParams,
+                 tau: float = SOFT_TAU, precision: str = "f32", threads: int = 1):
+    """Soft deposits (FP64 raster [H, W]) of every particle; weights per release entry."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    creal, npr = _real(precision)
+    h = np.ascontiguousarray(h, dtype=npr)
+    H, W = h.shape
+    cells = np.ascontiguousarray(cells, dtype=np.uint32)
+    weights = np.ascontiguousarray(weights, dtype=np.float64)
+    p = params.to_c(precision)
+    parts = [(c, w) for c, w in zip(np.array_split(cells, threads), np.array_split(weights, threads)) if c.size] \
+        or [(cells, weights)]
+
+    def one(cw):
+        c, w = cw
+        dep = np.zeros((H, W), np.float64)
+        st = Stats()
+        rc = lib(precision).orc_soft_forward(_ptr(h), ctypes.c_int32(W), ctypes.c_int32(H), creal(cs), _ptr(c),
+                                             ctypes.c_uint32(c.size), _ptr(w), ctypes.byref(p),
+                                             ctypes.c_double(tau), _ptr(dep), ctypes.byref(st))
+        _check(rc, "orc_soft_forward")
+        return dep, st.as_dict()
+
+    with ThreadPoolExecutor(len(parts)) as ex:
+        out = list(ex.map(one, parts))
+    dep = out[0][0]
+    for d, _ in out[1:]:
+        dep += d
+    stats = {k: sum(o[1][k] for o in out) for k in out[0][1]}
+    return dep, stats
+
+
+def soft_gradient(h: np.ndarray, cs: float, cells: np.ndarray, weights: np.ndarray, params: SimParams,
+                  G: np.ndarray, tau: float = SOFT_TAU, precision: str = "f32", threads: int = 1):
+    """FP64 reverse-mode gradient of sum(G * D): (d/dlog mu, d/dlog k), d/dw per release entry."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    creal, npr = _real(precision)
+    h = np.ascontiguousarray(h, dtype=npr)
+    H, W = h.shape
+    cells = np.ascontiguousarray(cells, dtype=np.uint32)
+    weights = np.ascontiguousarray(weights, dtype=np.float64)
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    p = params.to_c(precision)
+    idx = [i for i in np.array_split(np.arange(cells.size), threads) if i.size] or [np.arange(0)]
+
+    def one(ix):
+        c = np.ascontiguousarray(cells[ix])
+        w = np.ascontiguousarray(weights[ix])
+        gt = np.zeros(2, np.float64)
+        gw = np.zeros(c.size, np.float64)
+        rc = lib(precision).orc_soft_gradient(_ptr(h), ctypes.c_int32(W), ctypes.c_int32(H), creal(cs), _ptr(c),
+                                              ctypes.c_uint32(c.size), _ptr(w), ctypes.byref(p),
+                                              ctypes.c_double(tau), _ptr(G), _ptr(gt), _ptr(gw))
+        _check(rc, "orc_soft_gradient")
+        return ix, gt, gw
+
+    with ThreadPoolExecutor(len(idx)) as ex:
+        out = list(ex.map(one, idx))
+    gtheta = np.zeros(2, np.float64)
+    gw = np.zeros(cells.size, np.float64)
+    for ix, gt, g in out:
+        gtheta += gt
+        gw[ix] = g
+    return gtheta, gw
+
+
 def finalize(maxe: np.ndarray, gravity: float = 9.81, precision: str = "f32") -> np.ndarray:
     creal, npr = _real(precision)
     m = np.ascontiguousarray(maxe, dtype=npr)

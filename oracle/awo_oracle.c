@@ -450,6 +450,185 @@ int orc_trace(const real* h, int32_t W, int32_t H, real cs, uint32_t cell, uint3
     return ORC_OK;
 }
 
+/* ------------------------------------------------------------------ */
+/* Soft-deposit mode (differentiable extension; the paper has no        */
+/* gradients).  The path is the same as in the hard mode (same FP32     */
+/* arithmetic in the FP32 build) but the energy no longer stops the     */
+/* particle: each particle carries a survival S (S_0 = 1) that decays   */
+/* by the logistic function of its energy-line height,                  */
+/*   S_n = S_{n-1} * sigma(e_n / tau),  sigma(x) = 1 / (1 + exp(-x)),     */
+/* and deposits the mass it loses, w (S_{n-1} - S_n), at the cell of     */
+/* p_n.  The particle ends when it leaves the domain, reaches max_steps, */
+/* has no direction, or S_n < 1e-7; the remainder w S_last goes to the   */
+/* last cell reached, so a particle deposits exactly w.  Energy,         */
+/* survival and deposits are evaluated in FP64 here.                     */
+/* ------------------------------------------------------------------ */
+#define SOFT_S_MIN 1e-7
+
+typedef struct {
+    int64_t n;         /* moves made */
+    int64_t cap;       /* capacity of the arrays */
+    double* e;         /* e_1 .. e_n */
+    double* S;         /* S_1 .. S_n */
+    int64_t* cell;     /* cell of p_0 .. p_n (n + 1 entries) */
+} soft_path;
+
+/* One soft particle: fills path (when non-null) and returns the number
+ * of moves.  The direction and positions follow run_trajectory exactly. */
+static int64_t soft_particle(const real* h, int32_t W, int32_t H, real cs, uint32_t cell, uint32_t j,
+                             const orc_params* p, double tau, soft_path* sp)
+{
+    const real P = p->persistence, R = p->randomness, s = p->step_scale;
+    const real oneP = (real)1 - P;
+    const real D = s * cs;
+    const double kD = (double)p->drag_k * (double)D, muD = (double)p->mu * (double)D;
+
+    real u = (real)(cell % (uint32_t)W), v = (real)(cell / (uint32_t)W);
+    footprint f = take_footprint(h, W, H, u, v);
+    double z = (double)bilinear_height(&f);
+    double e = 0.0, S = 1.0;
+    real dx, dy;
+    downslope(&f, (real)0, (real)0, &dx, &dy);
+    if (sp) sp->cell[0] = cell_of(W, u, v);
+    int64_t n = 0;
+    while ((uint32_t)n < p->max_steps) {
+        real gx, gy;
+        f = take_footprint(h, W, H, u, v);
+        downslope(&f, dx, dy, &gx, &gy);
+        uint32_t wx, wy;
+        draw_pair(cell, j, (uint32_t)n, p->seed, &wx, &wy);
+        real xix = uniform_pm1(wx), xiy = uniform_pm1(wy);
+        real rx = (P * dx + oneP * gx) + R * xix;
+        real ry = (P * dy + oneP * gy) + R * xiy;
+        real r2 = rx * rx + ry * ry;
+        if (r2 == (real)0) break;
+        real inv = (real)1 / SQRT_RN(r2);
+        dx = rx * inv;
+        dy = ry * inv;
+        real u1 = u + s * dx, v1 = v + s * dy;
+        if (!(u1 >= (real)0 && u1 <= (real)(W - 1) && v1 >= (real)0 && v1 <= (real)(H - 1))) break;
+        footprint f1 = take_footprint(h, W, H, u1, v1);
+        double z1 = (double)bilinear_height(&f1);
+        double e1 = (e - kD * e) + (z - z1) - muD;
+        double S1 = S / (1.0 + exp(-e1 / tau));
+        u = u1; v = v1; z = z1; e = e1; S = S1;
+        ++n;
+        if (sp) {
+            if (n >= sp->cap) return -1;
+            sp->e[n] = e;
+            sp->S[n] = S;
+            sp->cell[n] = cell_of(W, u, v);
+        }
+        if (S < SOFT_S_MIN) break;
+    }
+    if (sp) sp->n = n;
+    return n;
+}
+
+static int soft_path_alloc(soft_path* sp, uint32_t max_steps)
+{
+    sp->cap = (int64_t)max_steps + 2;
+    sp->e = (double*)malloc(sizeof(double) * sp->cap);
+    sp->S = (double*)malloc(sizeof(double) * sp->cap);
+    sp->cell = (int64_t*)malloc(sizeof(int64_t) * sp->cap);
+    if (!sp->e || !sp->S || !sp->cell) {
+        free(sp->e); free(sp->S); free(sp->cell);
+        return ORC_ENOMEM;
+    }
+    sp->e[0] = 0.0;
+    sp->S[0] = 1.0;
+    return ORC_OK;
+}
+
+static void soft_path_free(soft_path* sp) { free(sp->e); free(sp->S); free(sp->cell); }
+
+/* Soft deposits of every particle of every listed release cell, weight
+ * weight[c] per particle of entry c, accumulated into deposit (FP64, W*H). */
+int orc_soft_forward(const real* h, int32_t W, int32_t H, real cs, const uint32_t* cells, uint32_t n_cells,
+                     const double* weight, const orc_params* p, double tau, double* deposit, orc_stats* st)
+{
+    int rc = check_params(W, H, cs, p);
+    if (rc) return rc;
+    if (!(tau > 0)) return ORC_EINVAL;
+    soft_path sp;
+    if (soft_path_alloc(&sp, p->max_steps)) return ORC_ENOMEM;
+    for (uint32_t c = 0; c < n_cells; ++c) {
+        if ((int64_t)cells[c] >= (int64_t)W * H) { soft_path_free(&sp); return ORC_EINVAL; }
+        for (uint32_t j = 0; j < p->traj_per_cell; ++j) {
+            soft_particle(h, W, H, cs, cells[c], j, p, tau, &sp);
+            double w = weight[c];
+            for (int64_t m = 1; m <= sp.n; ++m) deposit[sp.cell[m]] += w * (sp.S[m - 1] - sp.S[m]);
+            deposit[sp.cell[sp.n]] += w * sp.S[sp.n];
+            if (st) { st->n_traj++; st->total_steps += (uint64_t)sp.n; }
+        }
+    }
+    soft_path_free(&sp);
+    return ORC_OK;
+}
+
+/* Reverse-mode gradient (FP64) of L = sum_cells G_c D_c-linearised loss:
+ * given G = dL/dD (W*H), returns dL/dlog(mu), dL/dlog(k) in grad_theta[0..1]
+ * (accumulated) and dL/dw per release-list entry (accumulated).  Per
+ * particle, the deposit functional J = w [sum_m G(c_m)(S_{m-1} - S_m) +
+ * G(c_n) S_n] is differentiated by the adjoint sweep
+ *   a_m     = dJ/dS_m (direct) = w (G(c_{m+1}) - G(c_m))  (m < n),  0 (m = n:
+ *             the last move's deposit plus the remainder is w S_{n-1})
+ *   abar_m  = a_m + sigma_{m+1} abar_{m+1}     (S_{m+1} = S_m sigma_{m+1})
+ *   lam_m   = dJ/de_m = abar_m S_{m-1} sigma'(e_m) + (1 - k D) lam_{m+1},
+ *             sigma'(e) = sigma (1 - sigma) / tau
+ *   dJ/dmu  = -D sum_m lam_m,   dJ/dk = -D sum_m lam_m e_{m-1}
+ * over the stored path (the path itself does not depend on mu, k, w). */
+int orc_soft_gradient(const real* h, int32_t W, int32_t H, real cs, const uint32_t* cells, uint32_t n_cells,
+                      const double* weight, const orc_params* p, double tau, const double* G,
+                      double* grad_theta, double* grad_weight)
+{
+    int rc = check_params(W, H, cs, p);
+    if (rc) return rc;
+    if (!(tau > 0)) return ORC_EINVAL;
+    soft_path sp;
+    if (soft_path_alloc(&sp, p->max_steps)) return ORC_ENOMEM;
+    const double D = (double)(p->step_scale * cs);
+    const double kD = (double)p->drag_k * D;
+    double* abar = (double*)malloc(sizeof(double) * sp.cap);
+    if (!abar) { soft_path_free(&sp); return ORC_ENOMEM; }
+    for (uint32_t c = 0; c < n_cells; ++c) {
+        if ((int64_t)cells[c] >= (int64_t)W * H) { free(abar); soft_path_free(&sp); return ORC_EINVAL; }
+        const double w = weight[c];
+        for (uint32_t j = 0; j < p->traj_per_cell; ++j) {
+            soft_particle(h, W, H, cs, cells[c], j, p, tau, &sp);
+            const int64_t n = sp.n;
+            /* dJ/dw */
+            double jw = 0.0;
+            for (int64_t m = 1; m <= n; ++m) jw += G[sp.cell[m]] * (sp.S[m - 1] - sp.S[m]);
+            jw += G[sp.cell[n]] * sp.S[n];
+            grad_weight[c] += jw;
+            /* adjoint of S_m, backwards: J depends on S_m directly through
+             * w (G(c_{m+1}) - G(c_m)) (or w G(c_n) at the end) and through
+             * S_{m+1} = S_m sigma_{m+1} */
+            for (int64_t m = n; m >= 1; --m) {
+                double direct = (m < n) ? w * (G[sp.cell[m + 1]] - G[sp.cell[m]]) : 0.0;
+                double sig_next = (m < n) ? sp.S[m + 1] / sp.S[m] : 0.0;
+                abar[m] = direct + ((m < n) ? sig_next * abar[m + 1] : 0.0);
+            }
+            /* adjoint of e_m: S_m = S_{m-1} sigma(e_m / tau) and e_{m+1} = e_m (1 - kD) + ... */
+            double lam_next = 0.0, dmu = 0.0, dk = 0.0;
+            for (int64_t m = n; m >= 1; --m) {
+                double sig = sp.S[m] / sp.S[m - 1];
+                double dsig = sig * (1.0 - sig) / tau;
+                double lam = abar[m] * sp.S[m - 1] * dsig + (1.0 - kD) * lam_next;
+                dmu += -D * lam;
+                dk += -D * lam * sp.e[m - 1];
+                lam_next = lam;
+            }
+            grad_theta[0] += (double)p->mu * dmu;   /* d/dlog(mu) = mu d/dmu */
+            grad_theta[1] += (double)p->drag_k * dk;
+        }
+    }
+    free(abar);
+    soft_path_free(&sp);
+    return ORC_OK;
+}
+
 /* c'. Velocity indicator per cell from the maximum energy-line height  */
 /* (Fig. 4 caption: the colour encodes Z^delta_max, read as velocity):  */
 /* vel = sqrt((2 g) * maxe).                                            */
