@@ -62,7 +62,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["awo", "reference"], default="awo")
-    ap.add_argument("--workload", choices=["large", "mid", "tiny", "batched", "served"], default="large")
+    ap.add_argument("--workload", choices=["large", "mid", "tiny", "batched", "served", "diff"], default="large")
     ap.add_argument("--batch-n", type=int, default=64, help="regions of the batched/served workload")
     ap.add_argument("--rate", type=float, default=200.0, help="Poisson arrival rate of the served workload (1/s)")
     ap.add_argument("--crop", type=int, default=0, help="use the top-left N x N crop of the workload's DEM")
@@ -507,6 +507,55 @@ def run_served(args, R: Ranks):
         print(json.dumps(line), flush=True)
 
 
+def run_diff(args, R: Ranks):
+    """Differentiable workload: soft deposits on a 1024^2 fBm DEM, target at
+    hidden friction parameters, L2 loss; forward and adjoint timed with CUDA
+    events; the gradient checked against central differences (h = 1e-3)."""
+    import torch
+
+    import paper_2506_23364_gb300 as awo
+    from paper_2506_23364_gb300 import inputs
+
+    n = 1024
+    dem = inputs.quantise_dm(inputs.fbm(n, 0.8, seed=3, relief=3000.0 * (n / 2048.0) ** 0.8))
+    prob = awo.SoftOverlay(dem, inputs.CELL_SIZE_M, inputs.MID_RELEASE_DEG, traj_per_cell=128, max_steps=2048,
+                           seed=0, device=R.device)
+    w = torch.from_numpy(np.random.default_rng(3).uniform(0.5, 1.5, prob.n_cells).astype(np.float32)).to(R.device)
+    mu0, k0 = float(np.tan(np.deg2rad(25.0))), 1e-3
+    Dstar = prob.forward_raw(mu0 * 1.2, k0 * 0.8, w)
+    loss = lambda mu, k: float(((prob.forward_raw(mu, k, w) - Dstar) ** 2).sum())
+    fwd, bwd = [], []
+    for it in range(args.warmup + args.steps):
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record()
+        D = prob.forward_raw(mu0, k0, w)
+        b.record()
+        gt, gw = prob.backward_raw(mu0, k0, w, 2.0 * (D - Dstar))
+        c.record()
+        c.synchronize()
+        if it >= args.warmup:
+            fwd.append(a.elapsed_time(b))
+            bwd.append(b.elapsed_time(c))
+    g = gt.cpu().tolist()
+    h = 1e-3
+    fd = [(loss(mu0 * np.exp(h), k0) - loss(mu0 * np.exp(-h), k0)) / (2 * h),
+          (loss(mu0, k0 * np.exp(h)) - loss(mu0, k0 * np.exp(-h))) / (2 * h)]
+    st = prob.stats.cpu().tolist()
+    line = {"metric": "differentiable soft-deposit overlay: forward + adjoint ms", "value":
+            statistics.median(fwd) + statistics.median(bwd), "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "dtype": "f32 (f64 gradient reductions)",
+            "data": "synthetic (seeded fBm, uint16 dm)",
+            "config": {"workload": "diff-fbm-1024", "release_cells": prob.n_cells, "traj_per_cell": 128,
+                       "max_steps": 2048, "theta_star": "(1.2 mu0, 0.8 k0)", "tau_m": prob.tau},
+            "forward_ms": statistics.median(fwd), "backward_ms": statistics.median(bwd),
+            "particles": st[1], "moves": st[0],
+            "grad_log_mu": g[0], "grad_log_k": g[1], "fd_log_mu": fd[0], "fd_log_k": fd[1],
+            "fd_rel_err": [abs(g[0] - fd[0]) / abs(fd[0]), abs(g[1] - fd[1]) / abs(fd[1])],
+            "grad_w_norm": float(gw.norm())}
+    if R.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args, R: Ranks):
     """The CPU oracle on the host cores: each step a bounded random sample of
     the workload's release cells (all particles of each)."""
@@ -561,6 +610,8 @@ def main():
             run_batched(args, R)
         elif args.workload == "served":
             run_served(args, R)
+        elif args.workload == "diff":
+            run_diff(args, R)
         else:
             run_awo(args, R)
     finally:

@@ -260,6 +260,48 @@ awo_status awo_tune_batched(const awo_sim_request* reqs, int32_t n_req, void* d_
                             void* stream, awo_tuning* best, float* best_ms);
 
 /*
+ * c (soft). Soft-deposit particles and their gradient -- a differentiable
+ * variant of the trajectory node for fitting friction parameters and release
+ * weights (the paper has no gradients; this mode is this library's).
+ * Each particle follows exactly the path of awo_simulate (same direction and
+ * move arithmetic, same Philox streams) but its energy does not stop it: it
+ * carries a survival S_0 = 1, S_n = S_{n-1} * sigma(e_n / tau) with
+ * sigma(x) = 1 / (1 + exp(-x)) (FP32, expf), deposits w (S_{n-1} - S_n) at
+ * the cell of p_n, and ends when it leaves the grid, has no direction,
+ * reaches max_steps, or S_n < 1e-7; the rest, w S_last, goes to the last cell
+ * reached.  w is the particle's release-cell weight (d_weight, FP32 per
+ * release-list entry).  e is FP32 as in awo_simulate, so results match an
+ * FP64 evaluation to FP32 rounding, not bit for bit.
+ *
+ * awo_soft_forward ACCUMULATES deposits into d_deposit (int64 per cell, fixed
+ * point: deposit = value * 2^-32; AWO_SIM_CLEAR_OUTPUTS zeroes it first).
+ * Each particle adds exactly round(w 2^32) (cumulative quantisation), so the
+ * raster is deterministic.  d_stats (nullable): total_steps, n_traj and
+ * n_rejected are set, the other fields are 0.
+ *
+ * awo_soft_backward, given G = dL/dD (FP32 per cell), overwrites
+ * d_grad_theta[0] = dL/dlog(mu), d_grad_theta[1] = dL/dlog(drag_k) (FP64) and
+ * d_grad_weight[i] = dL/dw_i (FP32, for the first min(*d_n_cells,
+ * n_cells_max) entries).  It recomputes every particle from its start with
+ * the same draws and carries forward tangents of the energy and survival
+ * (the path itself does not depend on mu, k or w), so it stores nothing per
+ * step.  Sums over particles are FP64.
+ * Both take a workspace of awo_soft_workspace_bytes(n_cells_max) bytes.
+ * tau > 0 in metres of energy-line height (1 m in the differentiable
+ * workload).
+ */
+size_t awo_soft_workspace_bytes(uint32_t n_cells_max);
+awo_status awo_soft_forward(const float* d_h, awo_grid g, const uint32_t* d_cells, const uint32_t* d_n_cells,
+                            uint32_t n_cells_max, const float* d_weight, const awo_sim_params* p, float tau,
+                            int64_t* d_deposit, awo_sim_stats* d_stats, void* d_ws, size_t ws_bytes, void* stream);
+awo_status awo_soft_backward(const float* d_h, awo_grid g, const uint32_t* d_cells, const uint32_t* d_n_cells,
+                             uint32_t n_cells_max, const float* d_weight, const awo_sim_params* p, float tau,
+                             const float* d_grad_deposit, double* d_grad_theta, float* d_grad_weight,
+                             void* d_ws, size_t ws_bytes, void* stream);
+/* Fixed-point deposits to FP64: d_out[i] = (double)d_q[i] * 2^-32. */
+awo_status awo_fixed_to_real(const int64_t* d_q, int64_t n, double* d_out, void* stream);
+
+/*
  * c'. Velocity indicator (Fig. 4: the colour encodes Z^delta_max, read as a
  * velocity): d_vel[i] = sqrt((2*gravity) * d_maxe[i]).  Exact.
  * d_vel may alias d_maxe.

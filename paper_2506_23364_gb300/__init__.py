@@ -106,6 +106,11 @@ def lib() -> ctypes.CDLL:
         "awo_simulate_batched_workspace_bytes": (sz, [vp, i32]),
         "awo_simulate_batched": (st, [vp, i32, vp, vp, vp, sz, vp]),
         "awo_tune_batched": (st, [vp, i32, vp, sz, vp, vp, vp]),
+        "awo_soft_workspace_bytes": (sz, [u32]),
+        "awo_soft_forward": (st, [vp, Grid, vp, vp, u32, vp, ctypes.POINTER(SimParams), f32, vp, vp, vp, sz, vp]),
+        "awo_soft_backward": (st, [vp, Grid, vp, vp, u32, vp, ctypes.POINTER(SimParams), f32, vp, vp, vp, vp, sz,
+                                   vp]),
+        "awo_fixed_to_real": (st, [vp, ctypes.c_int64, vp, vp]),
         "awo_probe_l2_gather": (st, [vp, u32, u32, vp, vp]),
         "awo_probe_l2_red": (st, [vp, u32, u32, vp]),
         "awo_probe_threads": (ctypes.c_uint64, []),
@@ -283,6 +288,51 @@ def awo_tune_batched(reqs, ws: torch.Tensor, stream=None) -> tuple[Tuning, float
     return best, float(ms.value)
 
 
+def awo_soft_workspace_bytes(n_cells_max: int) -> int:
+    return int(lib().awo_soft_workspace_bytes(int(n_cells_max)))
+
+
+def _cells_args(cells, n_cells_dev, n_cells_max):
+    cp = None
+    if cells is not None:
+        if cells.dtype not in (torch.int32, torch.uint32):
+            raise TypeError("cells must be int32 or uint32")
+        cp = _dev(cells, cells.dtype, n_cells_max, "cells")
+    nd = _dev(n_cells_dev, n_cells_dev.dtype, 1, "n_cells_dev") if n_cells_dev is not None else None
+    return cp, nd
+
+
+def awo_soft_forward(h: torch.Tensor, g: Grid, cells, n_cells_dev, n_cells_max: int, weight: torch.Tensor,
+                     params: SimParams, tau: float, deposit: torch.Tensor, stats: torch.Tensor | None,
+                     ws: torch.Tensor, stream=None):
+    """Soft deposits (int64 fixed point, 2^-32) of every particle; see awo.h."""
+    cp, nd = _cells_args(cells, n_cells_dev, n_cells_max)
+    _check(lib().awo_soft_forward(_dev(h, torch.float32, g.cells, "h"), g, cp, nd, int(n_cells_max),
+                                  _dev(weight, torch.float32, n_cells_max, "weight"), ctypes.byref(params),
+                                  float(tau), _dev(deposit, torch.int64, g.cells, "deposit"),
+                                  _dev(stats, torch.int64, 6, "stats") if stats is not None else None,
+                                  _dev(ws, torch.uint8, None, "ws"), ws.numel(), _stream(stream)), "awo_soft_forward")
+
+
+def awo_soft_backward(h: torch.Tensor, g: Grid, cells, n_cells_dev, n_cells_max: int, weight: torch.Tensor,
+                      params: SimParams, tau: float, grad_deposit: torch.Tensor, grad_theta: torch.Tensor,
+                      grad_weight: torch.Tensor, ws: torch.Tensor, stream=None):
+    """dL/dlog(mu), dL/dlog(k) (FP64 [2]) and dL/dw (FP32 per release entry) given dL/dD."""
+    cp, nd = _cells_args(cells, n_cells_dev, n_cells_max)
+    _check(lib().awo_soft_backward(_dev(h, torch.float32, g.cells, "h"), g, cp, nd, int(n_cells_max),
+                                   _dev(weight, torch.float32, n_cells_max, "weight"), ctypes.byref(params),
+                                   float(tau), _dev(grad_deposit, torch.float32, g.cells, "grad_deposit"),
+                                   _dev(grad_theta, torch.float64, 2, "grad_theta"),
+                                   _dev(grad_weight, torch.float32, n_cells_max, "grad_weight"),
+                                   _dev(ws, torch.uint8, None, "ws"), ws.numel(), _stream(stream)),
+           "awo_soft_backward")
+
+
+def awo_fixed_to_real(q: torch.Tensor, out: torch.Tensor, stream=None):
+    _check(lib().awo_fixed_to_real(_dev(q, torch.int64, None, "q"), q.numel(),
+                                   _dev(out, torch.float64, q.numel(), "out"), _stream(stream)), "awo_fixed_to_real")
+
+
 def awo_finalize(maxe: torch.Tensor, g: Grid, gravity: float, vel: torch.Tensor, stream=None):
     _check(lib().awo_finalize(_dev(maxe, torch.float32, g.cells, "maxe"), g, gravity,
                               _dev(vel, torch.float32, g.cells, "vel"), _stream(stream)), "awo_finalize")
@@ -341,3 +391,4 @@ def stats_dict(stats: torch.Tensor) -> dict:
 
 from .pipeline import Overlay  # noqa: E402  (re-export)
 from .batch import Batch  # noqa: E402  (re-export)
+from .differentiable import SoftDeposit, SoftOverlay  # noqa: E402  (re-export)

@@ -1,0 +1,85 @@
+"""Soft-deposit mode on the GPU: deposits against the oracle, the adjoint
+kernel's gradient against the oracle's FP64 reverse sweep and against central
+finite differences (h = 1e-3 in log-parameters), and the autograd.Function."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2506_23364_gb300 as awo
+from paper_2506_23364_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+MU0, K0 = math.tan(math.radians(25.0)), 1e-3
+
+
+@pytest.fixture(scope="module")
+def problem():
+    z = inputs.fbm(112, 0.8, seed=21, relief=900.0, m=97).astype(np.float32)
+    prob = awo.SoftOverlay(z, 10.0, (30.0, 50.0), traj_per_cell=16, max_steps=400, persistence=0.85,
+                           randomness=0.2, seed=5)
+    cells = prob.cells[: prob.n_cells].cpu().numpy().view(np.uint32)
+    w = np.random.default_rng(3).uniform(0.5, 1.5, cells.size).astype(np.float32)
+    op = lambda mu, k: oracle.SimParams(mu=mu, drag_k=k, persistence=0.85, randomness=0.2, traj_per_cell=16,
+                                        max_steps=400, seed=5)
+    return z, prob, cells, w, op
+
+
+def test_soft_forward_matches_oracle_and_conserves_mass(problem):
+    z, prob, cells, w, op = problem
+    assert cells.size > 200
+    wt = torch.from_numpy(w).cuda()
+    D = prob.forward_raw(MU0, K0, wt).cpu().numpy()
+    q = prob.q.cpu().numpy()
+    Wq = np.rint(w.astype(np.float64) * 2.0 ** 32).astype(np.int64)
+    assert int(q.sum()) == 16 * int(Wq.sum())  # every particle deposits exactly round(w 2^32)
+    Dref, st = oracle.soft_forward(z, 10.0, cells, w.astype(np.float64), op(MU0, K0), threads=8)
+    assert np.allclose(D, Dref, rtol=1e-4, atol=2e-5)
+    assert prob.stats.cpu().tolist()[1] == st["n_traj"]
+    D2 = prob.forward_raw(MU0, K0, wt).cpu().numpy()
+    assert np.array_equal(D, D2)
+
+
+def test_adjoint_matches_fp64_reverse_sweep(problem):
+    z, prob, cells, w, op = problem
+    wt = torch.from_numpy(w).cuda()
+    G = np.random.default_rng(9).normal(size=z.shape).astype(np.float32)
+    gt, gw = prob.backward_raw(MU0, K0, wt, torch.from_numpy(G).cuda())
+    gt, gw = gt.cpu().numpy(), gw.cpu().numpy()
+    rt, rw = oracle.soft_gradient(z, 10.0, cells, w.astype(np.float64), op(MU0, K0), G.astype(np.float64),
+                                  threads=8)
+    assert np.allclose(gt, rt, rtol=2e-3, atol=1e-6 * np.abs(rt).max()), (gt, rt)
+    assert np.allclose(gw, rw, rtol=2e-3, atol=1e-4 * np.abs(rw).max())
+
+
+def test_adjoint_matches_central_differences(problem):
+    z, prob, cells, w, op = problem
+    wt = torch.from_numpy(w).cuda()
+    Dstar = prob.forward_raw(MU0 * 1.2, K0 * 0.8, wt)
+    L = lambda mu, k: float(((prob.forward_raw(mu, k, wt) - Dstar) ** 2).sum())
+    D0 = prob.forward_raw(MU0, K0, wt)
+    gt, _ = prob.backward_raw(MU0, K0, wt, 2.0 * (D0 - Dstar))
+    gt = gt.cpu().numpy()
+    h = 1e-3
+    fd_mu = (L(MU0 * math.exp(h), K0) - L(MU0 * math.exp(-h), K0)) / (2 * h)
+    fd_k = (L(MU0, K0 * math.exp(h)) - L(MU0, K0 * math.exp(-h))) / (2 * h)
+    assert abs(gt[0] - fd_mu) <= 5e-3 * abs(fd_mu), (gt[0], fd_mu)
+    assert abs(gt[1] - fd_k) <= 5e-3 * abs(fd_k), (gt[1], fd_k)
+
+
+def test_autograd_function(problem):
+    z, prob, cells, w, op = problem
+    wt = torch.from_numpy(w).cuda()
+    Dstar = prob.forward_raw(MU0 * 1.2, K0 * 0.8, wt)
+    log_mu = torch.tensor(math.log(MU0), dtype=torch.float64, requires_grad=True)
+    log_k = torch.tensor(math.log(K0), dtype=torch.float64, requires_grad=True)
+    wr = wt.clone().requires_grad_(True)
+    D = prob.deposit(log_mu, log_k, wr)
+    loss = ((D - Dstar) ** 2).sum()
+    loss.backward()
+    gt, gw = prob.backward_raw(MU0, K0, wt, 2.0 * (D.detach() - Dstar))
+    assert torch.allclose(torch.stack([log_mu.grad, log_k.grad]), gt.cpu(), rtol=1e-12, atol=0)
+    assert torch.equal(wr.grad, gw)
