@@ -62,7 +62,8 @@ def _args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["awo", "reference"], default="awo")
-    ap.add_argument("--workload", choices=["large", "mid", "tiny", "batched", "served", "diff"], default="large")
+    ap.add_argument("--workload", choices=["large", "mid", "tiny", "batched", "served", "diff", "parabola"],
+                    default="large")
     ap.add_argument("--batch-n", type=int, default=64, help="regions of the batched/served workload")
     ap.add_argument("--rate", type=float, default=200.0, help="Poisson arrival rate of the served workload (1/s)")
     ap.add_argument("--crop", type=int, default=0, help="use the top-left N x N crop of the workload's DEM")
@@ -556,6 +557,50 @@ def run_diff(args, R: Ranks):
         print(json.dumps(line), flush=True)
 
 
+def run_parabola(args, R: Ranks):
+    """Parabola-shaped stand-in (501 x 151, three given release cells, 2048
+    particles each): the whole workflow per step, from the device-resident DEM
+    and release mask."""
+    import torch
+
+    import paper_2506_23364_gb300 as awo
+    from paper_2506_23364_gb300 import inputs
+
+    w = inputs.parabola()
+    ov = awo.Overlay(w.width, w.height, w.cell_size, quantised=False, levels=1, device=R.device)
+    ov.load_dem(w.dem_f32)
+    mask = torch.from_numpy(inputs.parabola_release_mask()).to(R.device)
+    p = awo.SimParams.make(mu=w.mu, persistence=w.persistence, randomness=w.randomness,
+                           traj_per_cell=w.traj_per_cell, max_steps=w.max_steps, seed=w.seed)
+
+    def step():
+        ov.terrain_from_mask(mask)
+        ov.simulate(p)
+        ov.overlay(w.gravity)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        step()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    st = ov.stats_dict()
+    line = {"metric": "ms per overlay, parabola-shaped stand-in", "value": statistics.median(ts), "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
+            "data": "synthetic parabola-shaped slope (stand-in; the paper's dataset is not available)",
+            "config": dict(w.describe(), release="3 given cells (mask)"),
+            "vs_baseline": None, "context": "paper Table 1: weBIGeo 13.5 ms on an RTX 3070 (WebGPU) for its "
+                                             "parabola dataset; different geometry and hardware",
+            "particles": st["n_traj"], "moves": st["total_steps"], "min_ms": min(ts)}
+    if R.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args, R: Ranks):
     """The CPU oracle on the host cores: each step a bounded random sample of
     the workload's release cells (all particles of each)."""
@@ -612,6 +657,8 @@ def main():
             run_served(args, R)
         elif args.workload == "diff":
             run_diff(args, R)
+        elif args.workload == "parabola":
+            run_parabola(args, R)
         else:
             run_awo(args, R)
     finally:

@@ -127,6 +127,15 @@ awo_status awo_release(const float* d_tan2, awo_grid g, double slope_lo_deg, dou
                        void* d_ws, size_t ws_bytes, void* stream);
 
 /*
+ * b'. Release cells from a caller's mask (Sec. 5.2: known release points,
+ * e.g. of historic avalanches, provided as a pre-computed texture).  Exact:
+ * d_cells receives, in increasing order, the indices i with d_mask[i] != 0;
+ * d_n their number.  Same workspace as awo_release.
+ */
+awo_status awo_release_from_mask(const uint8_t* d_mask, awo_grid g, uint32_t* d_cells, uint32_t* d_n,
+                                 void* d_ws, size_t ws_bytes, void* stream);
+
+/*
  * Release selection without a caller-provided workspace.  (The paper has no
  * counterpart: this is a library convenience.)  Some callers cannot hand the
  * library any extra device memory: a plug-in inside a host application, such
@@ -319,6 +328,53 @@ awo_status awo_finalize(const float* d_maxe, awo_grid g, float gravity, float* d
  */
 awo_status awo_overlay_lod(const uint32_t* d_count, const float* d_vel, awo_grid g, int32_t levels,
                            uint32_t* const* d_count_lv, float* const* d_vel_lv, void* stream);
+
+/*
+ * Compose (Sec. 3: the compose pass alpha-blends the data-driven overlay over
+ * the base map; Fig. 4: colour encodes Z^delta_max, read as velocity).
+ * Exact.  Per texel: x = d_value[i] clamped to [value[0], value[n_stops-1]];
+ * k the segment with value[k] <= x (last segment for the top stop);
+ * t = (x - value[k]) / (value[k+1] - value[k]); per channel
+ * c = rgb[k] + t * (rgb[k+1] - rgb[k]); a = alpha if d_count[i] >= count_min
+ * else 0.  With d_base_rgba: out.rgb = rint(a*c + (1-a)*base.rgb),
+ * out.a = base.a; without: out.rgb = rint(c), out.a = rint(255*a).  FP32,
+ * no fused multiply-add, round half to even, clamped to [0, 255].
+ * d_value: float [H*W]; d_count: uint32 [H*W]; RGBA8 buffers [4*H*W],
+ * 4-byte aligned.  Requires 2 <= n_stops <= 16, strictly increasing values,
+ * alpha in [0, 1].
+ */
+typedef struct {
+    int32_t n_stops;
+    float value[16];
+    uint8_t rgb[16][3];
+    uint8_t pad[4];
+    float alpha;
+    uint32_t count_min;
+} awo_colormap;
+awo_status awo_compose(const float* d_value, const uint32_t* d_count, awo_grid g, const awo_colormap* cm,
+                       const uint8_t* d_base_rgba, uint8_t* d_out_rgba, void* stream);
+
+/*
+ * Snow cover (Sec. 5.1: snow line altitude, maximum steepness and blending
+ * factors; snow-covered texels white, alpha the blending factor).  Exact.
+ * With nz the normal's z component (awo_normals' third plane, the cosine of
+ * the slope angle):
+ *   alpha = smoothstep(L - b/2, L + b/2, h) * smoothstep(cos(m + c/2), cos(m - c/2), nz)
+ * L = snow_line_m, b = blend_alt_m, m = max_slope_deg, c = blend_slope_deg
+ * (slope bounds clamped to [0, 90] degrees); the four edges computed in
+ * double on the host and rounded to float once; smoothstep(e0, e1, x) =
+ * t*t*(3 - 2*t), t = clamp((x - e0) / (e1 - e0), 0, 1), a step x >= e0 when
+ * e0 == e1.  Outputs: d_alpha float [H*W] and/or d_rgba (255, 255, 255,
+ * rint(255*alpha)) [4*H*W].
+ */
+typedef struct {
+    float snow_line_m;
+    float blend_alt_m;
+    float max_slope_deg;
+    float blend_slope_deg;
+} awo_snow_params;
+awo_status awo_snow_cover(const float* d_h, const float* d_nz, awo_grid g, const awo_snow_params* p,
+                          float* d_alpha, uint8_t* d_rgba, void* stream);
 
 #ifdef __cplusplus
 }

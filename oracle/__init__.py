@@ -368,3 +368,48 @@ def simulate_threaded(h: np.ndarray, cs: float, cells: np.ndarray, params: SimPa
         count64 += c
         np.maximum(maxe, m, out=maxe)
     return count64, maxe, stats
+
+
+
+# ----------------------------------------------------------------------------
+# Compose and snow cover
+# ----------------------------------------------------------------------------
+class _Colormap(ctypes.Structure):
+    _fields_ = [("n_stops", ctypes.c_int32), ("value", ctypes.c_float * 16), ("rgb", (ctypes.c_uint8 * 3) * 16),
+                ("pad", ctypes.c_uint8 * 4), ("alpha", ctypes.c_float), ("count_min", ctypes.c_uint32)]
+
+
+def compose(value: np.ndarray, count: np.ndarray, stops, alpha: float, count_min: int, base: np.ndarray | None = None,
+            precision: str = "f32") -> np.ndarray:
+    """RGBA8 [..., 4] overlay colouring and alpha blend (see awo_oracle.c)."""
+    _, npr = _real(precision)
+    v = np.ascontiguousarray(value, dtype=npr)
+    c = np.ascontiguousarray(count, dtype=np.uint32)
+    cm = _Colormap()
+    cm.n_stops = len(stops)
+    for i, (x, rgb) in enumerate(stops):
+        cm.value[i] = float(x)
+        for k in range(3):
+            cm.rgb[i][k] = int(rgb[k])
+    cm.alpha = float(alpha)
+    cm.count_min = int(count_min)
+    out = np.empty(v.shape + (4,), np.uint8)
+    b = None if base is None else np.ascontiguousarray(base, dtype=np.uint8)
+    rc = lib(precision).orc_compose(_ptr(v), _ptr(c), ctypes.c_int64(v.size), ctypes.byref(cm), _ptr(b), _ptr(out))
+    _check(rc, "orc_compose")
+    return out
+
+
+def snow_cover(h: np.ndarray, nz: np.ndarray, snow_line: float, blend_alt: float, max_slope_deg: float,
+               blend_slope_deg: float, precision: str = "f32"):
+    """(alpha [H, W], RGBA8 [H, W, 4]) of the snow-cover overlay (see awo_oracle.c)."""
+    _, npr = _real(precision)
+    hh = np.ascontiguousarray(h, dtype=npr)
+    z = np.ascontiguousarray(nz, dtype=npr)
+    a = np.empty(hh.shape, npr)
+    rgba = np.empty(hh.shape + (4,), np.uint8)
+    rc = lib(precision).orc_snow_cover(_ptr(hh), _ptr(z), ctypes.c_int64(hh.size), ctypes.c_double(snow_line),
+                                       ctypes.c_double(blend_alt), ctypes.c_double(max_slope_deg),
+                                       ctypes.c_double(blend_slope_deg), _ptr(a), _ptr(rgba))
+    _check(rc, "orc_snow_cover")
+    return a, rgba

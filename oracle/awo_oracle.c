@@ -687,3 +687,102 @@ int orc_lod(const uint32_t* count, const real* vel, int32_t W, int32_t H, int32_
 
 /* Size of the real type this build computes in (4 or 8). */
 int orc_real_size(void) { return (int)sizeof(real); }
+
+/* ------------------------------------------------------------------ */
+/* Compose pass (Sec. 3: the overlay is alpha-blended over the base map; */
+/* Fig. 4: colour encodes Z^delta_max, read as velocity).  Per texel:    */
+/*   k: the ramp segment with value[k] <= x <= value[k+1] (x clamped to   */
+/*      the first and last stops),  t = (x - value[k]) / (value[k+1] -    */
+/*      value[k]),  c = rgb[k] + t (rgb[k+1] - rgb[k])  per channel;      */
+/*   a = alpha when count >= count_min, else 0;                          */
+/*   with a base: out.rgb = rint(a c + (1 - a) base.rgb), out.a = base.a; */
+/*   without:     out.rgb = rint(c), out.a = rint(255 a).                 */
+/* FP32 in the FP32 build, round half to even.                           */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int32_t n_stops;
+    float value[16];
+    uint8_t rgb[16][3];
+    uint8_t pad[4];
+    float alpha;
+    uint32_t count_min;
+} orc_colormap;
+
+static uint8_t to_u8(real x)
+{
+    if (!(x > (real)0)) return 0;
+    if (x > (real)255) return 255;
+    return (uint8_t)rint((double)x);
+}
+
+int orc_compose(const real* value, const uint32_t* count, int64_t n, const orc_colormap* cm, const uint8_t* base,
+                uint8_t* out)
+{
+    if (!cm || cm->n_stops < 2 || cm->n_stops > 16) return ORC_EINVAL;
+    for (int k = 0; k + 1 < cm->n_stops; ++k)
+        if (!(cm->value[k] < cm->value[k + 1])) return ORC_EINVAL;
+    const real alpha = (real)cm->alpha;
+    for (int64_t i = 0; i < n; ++i) {
+        real x = value[i];
+        const int last = cm->n_stops - 1;
+        if (!(x > (real)cm->value[0])) x = (real)cm->value[0];
+        if (x > (real)cm->value[last]) x = (real)cm->value[last];
+        int k = 0;
+        while (k + 1 < last && x >= (real)cm->value[k + 1]) ++k;
+        const real t = (x - (real)cm->value[k]) / ((real)cm->value[k + 1] - (real)cm->value[k]);
+        const real a = count[i] >= cm->count_min ? alpha : (real)0;
+        for (int ch = 0; ch < 3; ++ch) {
+            const real c0 = (real)cm->rgb[k][ch], c1 = (real)cm->rgb[k + 1][ch];
+            const real c = c0 + t * (c1 - c0);
+            if (base)
+                out[4 * i + ch] = to_u8(a * c + ((real)1 - a) * (real)base[4 * i + ch]);
+            else
+                out[4 * i + ch] = to_u8(c);
+        }
+        out[4 * i + 3] = base ? base[4 * i + 3] : to_u8((real)255 * a);
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Snow cover (Sec. 5.1: the user sets the snow-line altitude, the      */
+/* maximum steepness and blending factors; snow-covered texels are      */
+/* white with alpha the blending factor).  Per texel with height h and  */
+/* normal z-component nz (nz = cos of the slope angle):                 */
+/*   a_alt   = smoothstep(L - b/2, L + b/2, h)                           */
+/*   a_slope = smoothstep(cos(m + c/2), cos(m - c/2), nz)                */
+/*   alpha   = a_alt * a_slope                                           */
+/* smoothstep(e0, e1, x) = t t (3 - 2 t), t = clamp((x - e0)/(e1 - e0)), */
+/* a step (x >= e0) when e0 == e1.  The four edges are computed in FP64  */
+/* from the parameters and rounded to FP32 once.                         */
+/* ------------------------------------------------------------------ */
+static real smooth_step(real e0, real e1, real x)
+{
+    if (e1 == e0) return x >= e0 ? (real)1 : (real)0;
+    real t = (x - e0) / (e1 - e0);
+    if (t < (real)0) t = 0;
+    if (t > (real)1) t = 1;
+    return t * t * ((real)3 - (real)2 * t);
+}
+
+int orc_snow_cover(const real* h, const real* nz, int64_t n, double snow_line, double blend_alt, double max_slope_deg,
+                   double blend_slope_deg, real* alpha, uint8_t* rgba)
+{
+    if (!(blend_alt >= 0) || !(blend_slope_deg >= 0) || !(max_slope_deg >= 0) || !(max_slope_deg <= 90))
+        return ORC_EINVAL;
+    const double r = 3.14159265358979323846 / 180.0;
+    const real a0 = (real)(snow_line - 0.5 * blend_alt), a1 = (real)(snow_line + 0.5 * blend_alt);
+    double s_lo = max_slope_deg + 0.5 * blend_slope_deg, s_hi = max_slope_deg - 0.5 * blend_slope_deg;
+    if (s_lo > 90.0) s_lo = 90.0;
+    if (s_hi < 0.0) s_hi = 0.0;
+    const real c0 = (real)cos(s_lo * r), c1 = (real)cos(s_hi * r);
+    for (int64_t i = 0; i < n; ++i) {
+        real a = smooth_step(a0, a1, h[i]) * smooth_step(c0, c1, nz[i]);
+        alpha[i] = a;
+        if (rgba) {
+            rgba[4 * i + 0] = rgba[4 * i + 1] = rgba[4 * i + 2] = 255;
+            rgba[4 * i + 3] = to_u8((real)255 * a);
+        }
+    }
+    return ORC_OK;
+}

@@ -73,6 +73,35 @@ class Tuning(ctypes.Structure):
                 "refill": "warp" if self.refill == REFILL_WARP else "lane"}
 
 
+class Colormap(ctypes.Structure):
+    """awo_colormap: colour ramp (up to 16 stops) and overlay opacity."""
+    _fields_ = [("n_stops", ctypes.c_int32), ("value", ctypes.c_float * 16), ("rgb", (ctypes.c_uint8 * 3) * 16),
+                ("pad", ctypes.c_uint8 * 4), ("alpha", ctypes.c_float), ("count_min", ctypes.c_uint32)]
+
+    @classmethod
+    def make(cls, stops, alpha: float = 0.75, count_min: int = 1):
+        """stops: [(value, (r, g, b)), ...] with increasing values."""
+        cm = cls()
+        cm.n_stops = len(stops)
+        for i, (v, c) in enumerate(stops):
+            cm.value[i] = float(v)
+            for k in range(3):
+                cm.rgb[i][k] = int(c[k])
+        cm.alpha = float(alpha)
+        cm.count_min = int(count_min)
+        return cm
+
+
+# Velocity colour scale for the overlay (m/s): blue -> cyan -> green -> yellow -> red.
+VELOCITY_STOPS = [(0.0, (40, 40, 200)), (10.0, (0, 190, 230)), (25.0, (40, 200, 60)), (45.0, (250, 220, 0)),
+                  (70.0, (220, 30, 30))]
+
+
+class SnowParams(ctypes.Structure):
+    _fields_ = [("snow_line_m", ctypes.c_float), ("blend_alt_m", ctypes.c_float),
+                ("max_slope_deg", ctypes.c_float), ("blend_slope_deg", ctypes.c_float)]
+
+
 REFILL_LANE, REFILL_WARP = 0, 1
 BATCH_MAX = 128
 STATS_FIELDS = ("total_steps", "n_traj", "n_exited", "n_capped", "n_stopped", "n_rejected")
@@ -99,6 +128,7 @@ def lib() -> ctypes.CDLL:
         "awo_release_workspace_bytes": (sz, [Grid]),
         "awo_release": (st, [vp, Grid, f64, f64, vp, vp, vp, vp, sz, vp]),
         "awo_release_noalloc": (st, [vp, Grid, f64, f64, vp, vp, vp, vp]),
+        "awo_release_from_mask": (st, [vp, Grid, vp, vp, vp, sz, vp]),
         "awo_simulate_workspace_bytes": (sz, [u32]),
         "awo_simulate": (st, [vp, Grid, vp, vp, u32, ctypes.POINTER(SimParams), vp, vp, vp, vp, sz, vp]),
         "awo_finalize": (st, [vp, Grid, f32, vp, vp]),
@@ -111,6 +141,8 @@ def lib() -> ctypes.CDLL:
         "awo_soft_backward": (st, [vp, Grid, vp, vp, u32, vp, ctypes.POINTER(SimParams), f32, vp, vp, vp, vp, sz,
                                    vp]),
         "awo_fixed_to_real": (st, [vp, ctypes.c_int64, vp, vp]),
+        "awo_compose": (st, [vp, vp, Grid, ctypes.POINTER(Colormap), vp, vp, vp]),
+        "awo_snow_cover": (st, [vp, vp, Grid, ctypes.POINTER(SnowParams), vp, vp, vp]),
         "awo_probe_l2_gather": (st, [vp, u32, u32, vp, vp]),
         "awo_probe_l2_red": (st, [vp, u32, u32, vp]),
         "awo_probe_threads": (ctypes.c_uint64, []),
@@ -189,6 +221,17 @@ def awo_release(tan2: torch.Tensor, g: Grid, slope_lo_deg: float, slope_hi_deg: 
                              _dev(mask, torch.uint8, c, "mask"), _dev(cells, cells.dtype, c, "cells"),
                              _dev(n, n.dtype, 1, "n"), _dev(ws, torch.uint8, None, "ws"), ws.numel(),
                              _stream(stream)), "awo_release")
+
+
+def awo_release_from_mask(mask: torch.Tensor, g: Grid, cells: torch.Tensor, n: torch.Tensor, ws: torch.Tensor,
+                          stream=None):
+    """Ordered release list from a caller's uint8 mask (known release areas)."""
+    c = g.cells
+    if cells.dtype not in (torch.int32, torch.uint32) or n.dtype not in (torch.int32, torch.uint32):
+        raise TypeError("cells and n must be int32 or uint32")
+    _check(lib().awo_release_from_mask(_dev(mask, torch.uint8, c, "mask"), g, _dev(cells, cells.dtype, c, "cells"),
+                                       _dev(n, n.dtype, 1, "n"), _dev(ws, torch.uint8, None, "ws"), ws.numel(),
+                                       _stream(stream)), "awo_release_from_mask")
 
 
 RELEASE_NOALLOC_MAX_CELLS = 8192 * 8192
@@ -331,6 +374,25 @@ def awo_soft_backward(h: torch.Tensor, g: Grid, cells, n_cells_dev, n_cells_max:
 def awo_fixed_to_real(q: torch.Tensor, out: torch.Tensor, stream=None):
     _check(lib().awo_fixed_to_real(_dev(q, torch.int64, None, "q"), q.numel(),
                                    _dev(out, torch.float64, q.numel(), "out"), _stream(stream)), "awo_fixed_to_real")
+
+
+def awo_compose(value: torch.Tensor, count: torch.Tensor, g: Grid, cm: Colormap, base_rgba: torch.Tensor | None,
+                out_rgba: torch.Tensor, stream=None):
+    """Colour-mapped overlay (RGBA8 [H, W, 4]), alpha-blended over base_rgba when given."""
+    c = g.cells
+    if count.dtype not in (torch.int32, torch.uint32):
+        raise TypeError("count must be int32 or uint32")
+    _check(lib().awo_compose(_dev(value, torch.float32, c, "value"), _dev(count, count.dtype, c, "count"), g,
+                             ctypes.byref(cm), _dev(base_rgba, torch.uint8, 4 * c, "base_rgba"),
+                             _dev(out_rgba, torch.uint8, 4 * c, "out_rgba"), _stream(stream)), "awo_compose")
+
+
+def awo_snow_cover(h: torch.Tensor, nz: torch.Tensor, g: Grid, p: SnowParams, alpha: torch.Tensor | None = None,
+                   rgba: torch.Tensor | None = None, stream=None):
+    c = g.cells
+    _check(lib().awo_snow_cover(_dev(h, torch.float32, c, "h"), _dev(nz, torch.float32, c, "nz"), g, ctypes.byref(p),
+                                _dev(alpha, torch.float32, c, "alpha"), _dev(rgba, torch.uint8, 4 * c, "rgba"),
+                                _stream(stream)), "awo_snow_cover")
 
 
 def awo_finalize(maxe: torch.Tensor, g: Grid, gravity: float, vel: torch.Tensor, stream=None):

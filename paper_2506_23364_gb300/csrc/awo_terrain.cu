@@ -186,6 +186,40 @@ __global__ void __launch_bounds__(RT_THREADS) k_release_scatter(const float* __r
     }
 }
 
+// Release cells given by a caller's mask (known release areas, Sec. 5.2:
+// "known release points encoded in a pre-computed texture"): per-tile counts
+// and ordered scatter of the cells whose mask byte is non-zero.
+__global__ void __launch_bounds__(RT_THREADS) k_mask_count(const uint8_t* __restrict__ mask, int64_t n,
+                                                           uint32_t* __restrict__ tile_count)
+{
+    const int64_t base = (int64_t)blockIdx.x * RT_TILE + (int64_t)threadIdx.x * RT_CELLS;
+    int cnt = 0;
+#pragma unroll
+    for (int k = 0; k < RT_CELLS; ++k)
+        if (base + k < n) cnt += __ldg(mask + base + k) != 0 ? 1 : 0;
+    int total;
+    block_exclusive_scan(cnt, &total);
+    if (threadIdx.x == 0) tile_count[blockIdx.x] = (uint32_t)total;
+}
+
+__global__ void __launch_bounds__(RT_THREADS) k_mask_scatter(const uint8_t* __restrict__ mask, int64_t n,
+                                                             const uint32_t* __restrict__ tile_offset,
+                                                             uint32_t* __restrict__ cells)
+{
+    const int64_t base = (int64_t)blockIdx.x * RT_TILE + (int64_t)threadIdx.x * RT_CELLS;
+    uint32_t bits = 0;
+#pragma unroll
+    for (int k = 0; k < RT_CELLS; ++k)
+        if (base + k < n && __ldg(mask + base + k) != 0) bits |= 1u << k;
+    int total;
+    int off = block_exclusive_scan(__popc(bits), &total) + (int)tile_offset[blockIdx.x];
+    while (bits) {
+        int k = __ffs(bits) - 1;
+        bits &= bits - 1;
+        cells[off++] = (uint32_t)(base + k);
+    }
+}
+
 static float tan2_of_degrees(double deg)
 {
     double t = tan(deg * (3.14159265358979323846 / 180.0));
@@ -312,5 +346,22 @@ extern "C" awo_status awo_release_noalloc(const float* d_tan2, awo_grid g, doubl
     k_release_mask<<<tiles, RT_THREADS, 0, s>>>(d_tan2, n, t_lo, t_hi, d_mask, tile_count);
     k_release_scan<<<1, 1024, 0, s>>>(tile_count, tiles, tile_offset, d_n);
     k_release_scatter<<<tiles, RT_THREADS, 0, s>>>(d_tan2, n, t_lo, t_hi, tile_offset, d_cells);
+    return launch_status();
+}
+
+extern "C" awo_status awo_release_from_mask(const uint8_t* d_mask, awo_grid g, uint32_t* d_cells, uint32_t* d_n,
+                                            void* d_ws, size_t ws_bytes, void* stream)
+{
+    if (!d_mask || !d_cells || !d_n || !d_ws || !grid_ok(g)) return AWO_EINVAL;
+    if ((((uintptr_t)d_ws) & 15u) != 0) return AWO_EINVAL;
+    if (ws_bytes < awo_release_workspace_bytes(g)) return AWO_ENOMEM;
+    const int64_t n = cells_of(g);
+    const int tiles = (int)((n + RT_TILE - 1) / RT_TILE);
+    uint32_t* tile_count = static_cast<uint32_t*>(d_ws);
+    uint32_t* tile_offset = tile_count + tiles;
+    cudaStream_t s = as_stream(stream);
+    k_mask_count<<<tiles, RT_THREADS, 0, s>>>(d_mask, n, tile_count);
+    k_release_scan<<<1, 1024, 0, s>>>(tile_count, tiles, tile_offset, d_n);
+    k_mask_scatter<<<tiles, RT_THREADS, 0, s>>>(d_mask, n, tile_offset, d_cells);
     return launch_status();
 }

@@ -255,3 +255,32 @@ def poisson_arrivals(n: int, rate_per_s: float, seed: int = 0) -> np.ndarray:
     """Arrival times (s) of a Poisson process of the given rate."""
     rng = np.random.default_rng(seed)
     return np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
+
+
+# ----------------------------------------------------------------------------
+# Parabola-shaped stand-in
+# ----------------------------------------------------------------------------
+def parabola_dem(W: int = 501, H: int = 151, cs: float = CELL_SIZE_M, L: int = 350,
+                 top_slope_deg: float = 35.0) -> np.ndarray:
+    """501 x 151 cells falling towards +x along a parabola that flattens out:
+    z = z_top (1 - x / L)^2 for x <= L and 0 beyond, with z_top chosen so the
+    slope at the top is top_slope_deg.  Stands in for the shape of the
+    paper's *parabola* dataset (Sec. 5.2, Table 1), whose exact geometry is
+    defined elsewhere and is not available here."""
+    z_top = np.tan(np.deg2rad(top_slope_deg)) * L * cs / 2.0
+    x = np.arange(W, dtype=np.float64)
+    prof = np.where(x <= L, z_top * (1.0 - x / L) ** 2, 0.0)
+    return np.broadcast_to(prof[None, :], (H, W)).astype(np.float32).copy()
+
+
+def parabola_release_mask(W: int = 501, H: int = 151) -> np.ndarray:
+    """Three release cells near the top of the slope (column 20, rows 65, 75, 85)."""
+    m = np.zeros((H, W), np.uint8)
+    m[[65, 75, 85], 20] = 1
+    return m
+
+
+def parabola() -> Workload:
+    w = Workload("parabola-standin-501x151", 501, 151, CELL_SIZE_M, 0.0, 0.0, traj_per_cell=2048,
+                 max_steps=2000, lod_levels=1, seed=0, dem_f32=parabola_dem())
+    return w

@@ -13,8 +13,8 @@ import numpy as np
 import torch
 
 from . import (AWO_OK, Grid, SimParams, awo_decode_u16, awo_finalize, awo_normals, awo_overlay_lod,
-               awo_release, awo_release_workspace_bytes, awo_simulate, awo_simulate_workspace_bytes, grid,
-               lod_shapes, stats_dict)
+               awo_release, awo_release_from_mask, awo_release_workspace_bytes, awo_simulate,
+               awo_simulate_workspace_bytes, grid, lod_shapes, stats_dict)
 
 SIM_CLEAR_OUTPUTS = 1
 
@@ -69,6 +69,13 @@ class Overlay:
         awo_normals(self.h, self.g, self.normal, self.tan2, self.slope, stream)
         awo_release(self.tan2, self.g, slope_lo_deg, slope_hi_deg, self.mask, self.cells, self.n_rel, self.ws_rel,
                     stream)
+
+    def terrain_from_mask(self, mask: torch.Tensor, decode_scale: float = 0.1, stream=None):
+        """a0-b': decode, normals and the release list from a caller's uint8 mask."""
+        if self.quantised:
+            awo_decode_u16(self.q, self.g, decode_scale, self.h, stream)
+        awo_normals(self.h, self.g, self.normal, self.tan2, self.slope, stream)
+        awo_release_from_mask(mask, self.g, self.cells, self.n_rel, self.ws_rel, stream)
 
     def simulate(self, params: SimParams, clear: bool = True, stream=None, cells=None, n_cells=None):
         """c: particles from the release list (or from the given cells)."""

@@ -1,0 +1,87 @@
+"""GPU parity of the next-row features: release from a caller's mask, the
+parabola-shaped stand-in workflow, compose colouring / blending and the
+snow-cover mask (all bit for bit against the oracle)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2506_23364_gb300 as awo
+from paper_2506_23364_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("shape,density", [((257, 300), 0.05), ((1, 1), 1.0), ((33, 129), 0.0), ((64, 64), 1.0),
+                                           ((1000, 999), 0.3)])
+def test_release_from_mask(shape, density):
+    H, W = shape
+    rng = np.random.default_rng(H + W)
+    m = (rng.random((H, W)) < density).astype(np.uint8) * rng.integers(1, 256, (H, W)).astype(np.uint8)
+    g = awo.grid(W, H, 10.0)
+    cells = torch.empty(H * W, dtype=torch.int32, device="cuda")
+    n = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = torch.empty(awo.awo_release_workspace_bytes(g), dtype=torch.uint8, device="cuda")
+    awo.awo_release_from_mask(torch.from_numpy(m).cuda(), g, cells, n, ws)
+    k = int(n.item())
+    want = np.flatnonzero(m.ravel())
+    assert k == want.size
+    assert np.array_equal(cells[:k].cpu().numpy().view(np.uint32), want.astype(np.uint32))
+
+
+def test_parabola_standin_bitexact():
+    w = inputs.parabola()
+    mask = inputs.parabola_release_mask()
+    ov = awo.Overlay(w.width, w.height, w.cell_size, quantised=False, levels=3)
+    ov.load_dem(w.dem_f32)
+    p = awo.SimParams.make(traj_per_cell=w.traj_per_cell, max_steps=w.max_steps, seed=w.seed)
+    ov.terrain_from_mask(torch.from_numpy(mask).cuda())
+    ov.simulate(p)
+    ov.overlay(w.gravity)
+    torch.cuda.synchronize()
+    got = ov.host_results()
+    cells = np.flatnonzero(mask.ravel()).astype(np.uint32)
+    c64, maxe, st = oracle.simulate_threaded(w.dem_f32, w.cell_size, cells,
+                                             oracle.SimParams(traj_per_cell=w.traj_per_cell, max_steps=w.max_steps))
+    assert np.array_equal(got["cells"], cells)
+    assert np.array_equal(got["count"], oracle.counts_u32(c64))
+    assert np.array_equal(got["maxe"], maxe)
+    assert got["stats"]["n_traj"] == 6144 and got["stats"]["total_steps"] == st["total_steps"]
+
+
+@pytest.mark.parametrize("with_base", [False, True])
+def test_compose_bitexact(with_base):
+    rng = np.random.default_rng(5)
+    H, W = 301, 257
+    v = rng.uniform(-5, 80, (H, W)).astype(np.float32)
+    v[rng.random((H, W)) < 0.05] = 10.0  # exactly on a stop
+    cnt = rng.integers(0, 5, (H, W)).astype(np.uint32)
+    base = rng.integers(0, 256, (H, W, 4)).astype(np.uint8) if with_base else None
+    g = awo.grid(W, H, 10.0)
+    cm = awo.Colormap.make(awo.VELOCITY_STOPS, alpha=0.7, count_min=2)
+    out = torch.empty((H, W, 4), dtype=torch.uint8, device="cuda")
+    awo.awo_compose(torch.from_numpy(v).cuda(), torch.from_numpy(cnt.view(np.int32)).cuda(), g, cm,
+                    torch.from_numpy(base).cuda() if with_base else None, out)
+    want = oracle.compose(v, cnt, awo.VELOCITY_STOPS, 0.7, 2, base)
+    assert np.array_equal(out.cpu().numpy(), want)
+
+
+def test_snow_cover_bitexact():
+    w = inputs.tiny()
+    h = w.dem_f32
+    H, W = h.shape
+    g = awo.grid(W, H, w.cell_size)
+    dh = torch.from_numpy(h).cuda()
+    nrm = torch.empty((3, H, W), dtype=torch.float32, device="cuda")
+    awo.awo_normals(dh, g, nrm, None, None)
+    p = awo.SnowParams(1500.0, 300.0, 36.0, 4.0)
+    a = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    rgba = torch.empty((H, W, 4), dtype=torch.uint8, device="cuda")
+    awo.awo_snow_cover(dh, nrm[2].contiguous(), g, p, a, rgba)
+    rn, _, _ = oracle.normals(h, w.cell_size)
+    ra, rrgba = oracle.snow_cover(h, rn[2], 1500.0, 300.0, 36.0, 4.0)
+    assert np.array_equal(a.cpu().numpy(), ra)
+    assert np.array_equal(rgba.cpu().numpy(), rrgba)
+    assert 0.0 < ra.mean() < 1.0
