@@ -62,8 +62,8 @@ def _args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["awo", "reference"], default="awo")
-    ap.add_argument("--workload", choices=["large", "mid", "tiny", "batched", "served", "diff", "parabola"],
-                    default="large")
+    ap.add_argument("--workload", choices=["large", "mid", "tiny", "batched", "served", "diff", "parabola",
+                                           "stages"], default="large")
     ap.add_argument("--batch-n", type=int, default=64, help="regions of the batched/served workload")
     ap.add_argument("--rate", type=float, default=200.0, help="Poisson arrival rate of the served workload (1/s)")
     ap.add_argument("--crop", type=int, default=0, help="use the top-left N x N crop of the workload's DEM")
@@ -601,6 +601,68 @@ def run_parabola(args, R: Ranks):
         print(json.dumps(line), flush=True)
 
 
+def run_stages(args, R: Ranks):
+    """Each streaming (HBM-bound) stage alone on the 8192^2 workload's rasters,
+    CUDA-event timed (median of --steps after --warmup), against the measured
+    HBM copy bandwidth, with the algorithmic bytes of the design doc."""
+    import torch
+
+    import paper_2506_23364_gb300 as awo
+    from paper_2506_23364_gb300 import inputs
+
+    w = _workload("large", args.crop)
+    ov = awo.Overlay(w.width, w.height, w.cell_size, quantised=True, levels=w.lod_levels, device=R.device,
+                     want_slope=True)
+    ov.load_dem(w.dem_u16)
+    p = awo.SimParams.make(traj_per_cell=w.traj_per_cell, max_steps=w.max_steps)
+    ov.run(w.slope_lo_deg, w.slope_hi_deg, p)
+    torch.cuda.synchronize()
+    n = w.width * w.height
+    n_rel = ov.n_release()
+    g = ov.g
+    cm = awo.Colormap.make(awo.VELOCITY_STOPS, alpha=0.7, count_min=1)
+    base = torch.zeros((w.height, w.width, 4), dtype=torch.uint8, device=R.device)
+    rgba = torch.empty_like(base)
+    alpha = torch.empty((w.height, w.width), dtype=torch.float32, device=R.device)
+    sp = awo.SnowParams(1500.0, 300.0, 36.0, 4.0)
+    nz = ov.normal[2]
+    lv_bytes = sum(c.numel() * 8 for c in ov.count_lv)
+    stages = [
+        ("decode", lambda: awo.awo_decode_u16(ov.q, g, 0.1, ov.h), 6 * n),
+        ("normals (+tan2)", lambda: awo.awo_normals(ov.h, g, ov.normal, ov.tan2, None), 20 * n),
+        ("normals (+tan2, slope_deg)", lambda: awo.awo_normals(ov.h, g, ov.normal, ov.tan2, ov.slope), 24 * n),
+        ("release (3 passes)", lambda: awo.awo_release(ov.tan2, g, w.slope_lo_deg, w.slope_hi_deg, ov.mask, ov.cells,
+                                                       ov.n_rel, ov.ws_rel), 9 * n + 4 * n_rel),
+        ("finalize", lambda: awo.awo_finalize(ov.maxe, g, 9.81, ov.vel), 8 * n),
+        ("mipmap (5 levels)", lambda: awo.awo_overlay_lod(ov.count, ov.vel, g, w.lod_levels, ov.count_lv, ov.vel_lv),
+         8 * n + lv_bytes),
+        ("compose over base", lambda: awo.awo_compose(ov.vel, ov.count, g, cm, base, rgba), 16 * n),
+        ("snow cover (alpha + rgba)", lambda: awo.awo_snow_cover(ov.h, nz, g, sp, alpha, rgba), 16 * n),
+    ]
+    peaks = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    rows = []
+    for name, fn, nbytes in stages:
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        ts = []
+        for _ in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = statistics.median(ts)
+        gbs = nbytes / (ms / 1e3) / 1e9
+        rows.append({"stage": name, "ms": ms, "alg_bytes": nbytes, "GB/s": gbs, "frac_hbm": gbs / hbm})
+    line = {"metric": "streaming stages at 8192^2: GB/s of algorithmic bytes vs measured HBM copy bandwidth",
+            "unit": "GB/s", "hbm_peak_gbs": hbm, "config": {"workload": w.name, "cells": n, "release_cells": n_rel},
+            "stages": rows}
+    if R.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args, R: Ranks):
     """The CPU oracle on the host cores: each step a bounded random sample of
     the workload's release cells (all particles of each)."""
@@ -659,6 +721,8 @@ def main():
             run_diff(args, R)
         elif args.workload == "parabola":
             run_parabola(args, R)
+        elif args.workload == "stages":
+            run_stages(args, R)
         else:
             run_awo(args, R)
     finally:
