@@ -53,7 +53,7 @@ ALG_OPS_PER_VISIT = 176
 # read + write of a 6144^2 crop launch, divided by its visits), keyed by the
 # SHA-256 prefix of the kernel source it was taken on; a changed kernel
 # reports traffic null until it is captured again.
-DRAM_BYTES_PER_VISIT: dict[str, float] = {"f7166d45e8e993c9": (268.830208e6 + 55.38176e6) / 1754008332}
+DRAM_BYTES_PER_VISIT: dict[str, float] = {"0623e1604391b370": (267.430656e6 + 54.800128e6) / 1754008332}
 
 
 def _args():

@@ -239,7 +239,9 @@ typedef struct {
 
 /* Launch shape of the batched particle kernel (the autotuner's search space).
  *   threads_per_block: 64, 128 or 256 (0 = 128)
- *   group_particles:   particles a warp takes per fetch, 32 .. 65536 (0 = 1024)
+ *   group_particles:   particles a warp takes per fetch, 32 .. 65536 (0 = chosen
+ *                      per launch: about all particles / (4 x the grid's warps),
+ *                      rounded down to a multiple of 32, within 32 .. 1024)
  *   refill: AWO_REFILL_LANE -- a lane starts the next particle as soon as its
  *           particle ends (trajectory per thread, continuously refilled);
  *           AWO_REFILL_WARP -- a warp starts 32 particles together and takes

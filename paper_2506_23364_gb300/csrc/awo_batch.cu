@@ -4,12 +4,12 @@
 // kernel's parameter block, so a launch needs no host-to-device copy and can
 // be captured in a CUDA graph.  Three kernels:
 //   k_batch_prepare  one block: release counts (possibly on the device), the
-//                    prefix sums of cells and of cell groups over requests,
-//                    zeroed counters;
+//                    chunk size, the prefix sums of cells and of particle
+//                    chunks over requests, zeroed counters;
 //   k_batch_starts   per release cell of every request: its start record and
 //                    the release visits of its particles;
-//   k_batch_simulate persistent: warps take cell groups from one global
-//                    counter over all requests.  A warp runs one request at
+//   k_batch_simulate persistent: warps take chunks of consecutive particles
+//                    from one global counter over all requests.  A warp runs one request at
 //                    a time; it switches only when all its lanes are idle,
 //                    which happens at request boundaries only, so the
 //                    request's constants are warp-uniform.  Lanes refill as
@@ -38,16 +38,18 @@ struct BatchReq {
     // work
     const uint32_t* cells;
     const uint32_t* n_cells_dev;
-    uint32_t n_cells_max, n_grid, N, cells_per_fetch;
+    uint32_t n_cells_max, n_grid, N;
     uint32_t k0, k1;      // Philox key (seed words)
     uint32_t starts_off;  // index of this request's first start record
 };
 
 struct BatchHeader {
-    unsigned long long next_group;
-    uint32_t group_prefix[AWO_BATCH_MAX + 1];
-    uint32_t cell_prefix[AWO_BATCH_MAX + 1];
+    unsigned long long next_chunk;                     // global work counter, in chunks
+    unsigned long long chunk_prefix[AWO_BATCH_MAX + 1];  // chunks before each request
+    uint32_t cell_prefix[AWO_BATCH_MAX + 1];           // start records before each request
     uint32_t n_cells[AWO_BATCH_MAX];
+    uint32_t chunk;                                    // particles per chunk
+    uint32_t pad;
     unsigned long long stats[AWO_BATCH_MAX][6];
 };
 constexpr size_t BATCH_HEADER_BYTES = ((sizeof(BatchHeader) + 255) / 256) * 256;
@@ -60,6 +62,8 @@ struct BatchArgs {
     BatchReq r[AWO_BATCH_MAX];
     KeysTable keys;  // round keys when every request has the same seed
     uint32_t n_req;
+    uint32_t group;      // particles per chunk (0 = chosen by k_batch_prepare)
+    uint32_t sim_warps;  // warps of the k_batch_simulate grid
     BatchHeader* hdr;
     CellStart* starts;
 };
@@ -102,7 +106,8 @@ __device__ __forceinline__ ReqRegs load_req(const BatchArgs& a, int r)
 }
 
 // Index r with prefix[r] <= g < prefix[r+1] (prefix has n + 1 entries).
-__device__ __forceinline__ int find_request(const uint32_t* prefix, int n, uint32_t g)
+template <typename T>
+__device__ __forceinline__ int find_request(const T* prefix, int n, T g)
 {
     int lo = 0, hi = n;  // invariant: prefix[lo] <= g < prefix[hi]
     while (hi - lo > 1) {
@@ -115,34 +120,48 @@ __device__ __forceinline__ int find_request(const uint32_t* prefix, int n, uint3
     return lo;
 }
 
+// Chunk size when the caller names none: a multiple of 32 in [32, 1024],
+// about total / (warps * 4), so that every warp gets several chunks.
+__device__ __forceinline__ uint32_t adaptive_chunk(unsigned long long total, uint32_t warps)
+{
+    unsigned long long c = total / ((unsigned long long)max(warps, 1u) * 4ull);
+    c = c < 32ull ? 32ull : (c > 1024ull ? 1024ull : c);
+    return (uint32_t)(c & ~31ull);
+}
+
 __global__ void __launch_bounds__(AWO_BATCH_MAX) k_batch_prepare(const __grid_constant__ BatchArgs a)
 {
-    __shared__ uint32_t s_nc[AWO_BATCH_MAX], s_ng[AWO_BATCH_MAX];
+    __shared__ uint32_t s_nc[AWO_BATCH_MAX];
+    __shared__ unsigned long long s_np[AWO_BATCH_MAX];
     const int t = threadIdx.x;
-    uint32_t nc = 0u, ng = 0u;
+    uint32_t nc = 0u;
     if (t < (int)a.n_req) {
         const BatchReq& q = a.r[t];
         nc = q.n_cells_max;
         if (q.n_cells_dev) nc = min(nc, *q.n_cells_dev);
         if (q.N == 0u) nc = 0u;  // no particles, no release visits
-        ng = (nc + q.cells_per_fetch - 1u) / q.cells_per_fetch;
         a.hdr->n_cells[t] = nc;
     }
     s_nc[t] = nc;
-    s_ng[t] = ng;
+    s_np[t] = t < (int)a.n_req ? (unsigned long long)nc * a.r[t].N : 0ull;
     for (int i = t; i < (int)a.n_req * 6; i += blockDim.x) (&a.hdr->stats[0][0])[i] = 0ull;
     __syncthreads();
     if (t == 0) {
-        uint32_t cs = 0u, gs = 0u;
+        unsigned long long total = 0ull;
+        for (int r = 0; r < (int)a.n_req; ++r) total += s_np[r];
+        const uint32_t chunk = a.group ? a.group : adaptive_chunk(total, a.sim_warps);
+        uint32_t cs = 0u;
+        unsigned long long gs = 0ull;
         for (int r = 0; r < (int)a.n_req; ++r) {
             a.hdr->cell_prefix[r] = cs;
-            a.hdr->group_prefix[r] = gs;
+            a.hdr->chunk_prefix[r] = gs;
             cs += s_nc[r];
-            gs += s_ng[r];
+            gs += (s_np[r] + chunk - 1u) / chunk;
         }
         a.hdr->cell_prefix[a.n_req] = cs;
-        a.hdr->group_prefix[a.n_req] = gs;
-        a.hdr->next_group = 0ull;
+        a.hdr->chunk_prefix[a.n_req] = gs;
+        a.hdr->chunk = chunk;
+        a.hdr->next_chunk = 0ull;
     }
 }
 
@@ -154,7 +173,7 @@ __global__ void __launch_bounds__(256) k_batch_starts(const __grid_constant__ Ba
     __syncthreads();
     const uint32_t total = s_cp[n];
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
-        const int r = find_request(s_cp, n, g);
+        const int r = find_request<uint32_t>(s_cp, n, g);
         const BatchReq& q = a.r[r];
         const uint32_t ci = g - s_cp[r];
         const uint32_t cell = __ldg(q.cells + ci);
@@ -167,43 +186,47 @@ __global__ void __launch_bounds__(256) k_batch_starts(const __grid_constant__ Ba
 template <int THREADS, bool WARP_REFILL, bool TABLE_KEYS>
 __global__ void __launch_bounds__(THREADS) k_batch_simulate(const __grid_constant__ BatchArgs a)
 {
-    __shared__ uint32_t s_gp[AWO_BATCH_MAX + 1];
+    __shared__ unsigned long long s_gp[AWO_BATCH_MAX + 1];
     const int n_req = (int)a.n_req;
-    for (int i = threadIdx.x; i <= n_req; i += blockDim.x) s_gp[i] = a.hdr->group_prefix[i];
+    for (int i = threadIdx.x; i <= n_req; i += blockDim.x) s_gp[i] = a.hdr->chunk_prefix[i];
     __syncthreads();
-    const uint32_t total_groups = s_gp[n_req];
+    const unsigned long long total_chunks = s_gp[n_req];
+    const uint32_t chunk = a.hdr->chunk;
 
     const int lane = threadIdx.x & 31;
     const unsigned lane_lt = (1u << lane) - 1u;
 
     int cr = -1;  // request of the warp (uniform)
     ReqRegs q = load_req(a, 0);
-    uint32_t cur_ci = 0u, cur_j = 0u, end_ci = 0u;
-    bool exhausted = (total_groups == 0u);
-    bool have_p = false;  // fetched group waiting for the warp to drain
+    // warp-uniform cursor: next particle of the request (t, and as (entry, j))
+    // and the end of the chunk
+    unsigned long long cur_t = 0ull, end_t = 0ull;
+    uint32_t cur_ci = 0u, cur_j = 0u;
+    bool exhausted = (total_chunks == 0ull);
+    bool have_p = false;  // fetched chunk waiting for the warp to drain
     int p_r = 0;
-    uint32_t p_ci = 0u, p_end = 0u;
+    unsigned long long p_t = 0ull, p_end = 0ull;
 
     AWO_LANE_STATE
 
     while (true) {
         const unsigned idle = __ballot_sync(0xffffffffu, !live);
         const bool can_refill = idle != 0u && (!WARP_REFILL || idle == 0xffffffffu);
-        if (can_refill && cur_ci >= end_ci && !exhausted && !have_p) {
+        if (can_refill && cur_t >= end_t && !exhausted && !have_p) {
             unsigned long long g = 0;
-            if (lane == 0) g = atomicAdd(&a.hdr->next_group, 1ull);
+            if (lane == 0) g = atomicAdd(&a.hdr->next_chunk, 1ull);
             g = __shfl_sync(0xffffffffu, g, 0);
-            if (g >= total_groups) {
+            if (g >= total_chunks) {
                 exhausted = true;
             } else {
-                p_r = find_request(s_gp, n_req, (uint32_t)g);
-                const uint32_t cpf = a.r[p_r].cells_per_fetch;
-                p_ci = ((uint32_t)g - s_gp[p_r]) * cpf;
-                p_end = min(p_ci + cpf, a.hdr->n_cells[p_r]);
+                p_r = find_request<unsigned long long>(s_gp, n_req, g);
+                const unsigned long long n_part = (unsigned long long)a.hdr->n_cells[p_r] * a.r[p_r].N;
+                p_t = (g - s_gp[p_r]) * chunk;
+                p_end = min(p_t + chunk, n_part);
                 have_p = true;
             }
         }
-        if (have_p && cur_ci >= end_ci && (p_r == cr || idle == 0xffffffffu)) {
+        if (have_p && cur_t >= end_t && (p_r == cr || idle == 0xffffffffu)) {
             if (p_r != cr) {
                 // all lanes are idle here; their positions are reset so that
                 // the loads of dead lanes stay inside the new request's grid
@@ -212,13 +235,14 @@ __global__ void __launch_bounds__(THREADS) k_batch_simulate(const __grid_constan
                 q = load_req(a, cr);
                 u = v = 0.0f;  // (fx .. h11 are not read before the first move)
             }
-            cur_ci = p_ci;
-            cur_j = 0u;
-            end_ci = p_end;
+            cur_t = p_t;
+            end_t = p_end;
+            cur_ci = (uint32_t)(p_t / q.N);  // one division per chunk
+            cur_j = (uint32_t)(p_t - (unsigned long long)cur_ci * q.N);
             have_p = false;
         }
-        if (can_refill && cur_ci < end_ci) {
-            const unsigned long long left = (unsigned long long)(end_ci - cur_ci) * q.N - cur_j;
+        if (can_refill && cur_t < end_t) {
+            const unsigned long long left = end_t - cur_t;
             const unsigned avail = left < 32ull ? (unsigned)left : 32u;
             const unsigned want = (unsigned)__popc(idle);
             const unsigned take = want < avail ? want : avail;
@@ -236,6 +260,7 @@ __global__ void __launch_bounds__(THREADS) k_batch_simulate(const __grid_constan
             my_traj += cap0 ? 1u : 0u;
             live = live || (ok && !cap0);
             advance(cur_ci, cur_j, take, q.N);
+            cur_t += take;
         }
         if (__ballot_sync(0xffffffffu, live) == 0u) {
             if (exhausted && !have_p) break;
@@ -323,7 +348,7 @@ extern "C" awo_status awo_simulate_batched(const awo_sim_request* reqs, int32_t 
     if ((((uintptr_t)d_ws) & 15u) != 0) return AWO_EINVAL;
     if (ws_bytes < BATCH_HEADER_BYTES + (size_t)total * sizeof(CellStart)) return AWO_ENOMEM;
     const int threads = (tuning && tuning->threads_per_block) ? tuning->threads_per_block : 128;
-    const uint32_t group = (tuning && tuning->group_particles) ? (uint32_t)tuning->group_particles : 1024u;
+    const uint32_t group = tuning ? (uint32_t)tuning->group_particles : 0u;
     const int refill = tuning ? tuning->refill : AWO_REFILL_LANE;
     cudaStream_t s = as_stream(stream);
 
@@ -358,7 +383,6 @@ extern "C" awo_status awo_simulate_batched(const awo_sim_request* reqs, int32_t 
         b.n_cells_max = q.n_cells_max;
         b.n_grid = (uint32_t)cells_of(q.grid);
         b.N = p->traj_per_cell;
-        b.cells_per_fetch = b.N >= group ? 1u : (group + b.N - 1u) / std::max(b.N, 1u);
         b.k0 = (uint32_t)(p->seed & 0xffffffffu);
         b.k1 = (uint32_t)(p->seed >> 32);
         b.starts_off = off;
@@ -378,10 +402,12 @@ extern "C" awo_status awo_simulate_batched(const awo_sim_request* reqs, int32_t 
         k1 += 0xBB67AE85u;
     }
 
-    k_batch_prepare<<<1, AWO_BATCH_MAX, 0, s>>>(a);
-    if (total > 0) k_batch_starts<<<stream_blocks((int64_t)total, 256), 256, 0, s>>>(a);
     BatchKernel k = pick_kernel(threads, refill, same_seed);
     const unsigned blocks = (unsigned)(sm_count() * blocks_per_sm(k, threads));
+    a.group = group;
+    a.sim_warps = blocks * (unsigned)(threads / 32);
+    k_batch_prepare<<<1, AWO_BATCH_MAX, 0, s>>>(a);
+    if (total > 0) k_batch_starts<<<stream_blocks((int64_t)total, 256), 256, 0, s>>>(a);
     k<<<blocks, threads, 0, s>>>(a);
     awo_status st = launch_status();
     if (st != AWO_OK) return st;
@@ -408,10 +434,10 @@ extern "C" awo_status awo_tune_batched(const awo_sim_request* reqs, int32_t n_re
         return AWO_ECUDA;
     }
     const int threads[] = {64, 128, 256};
-    const int groups[] = {256, 1024, 4096};
+    const int groups[] = {0, 256, 1024, 4096};  // 0: chosen from the particle count
     const int refills[] = {AWO_REFILL_LANE, AWO_REFILL_WARP};
     float best_t = 3.0e38f;
-    awo_tuning best_cfg = {128, 1024, AWO_REFILL_LANE, 0};
+    awo_tuning best_cfg = {128, 0, AWO_REFILL_LANE, 0};
     awo_status result = AWO_OK;
     for (int rf : refills)
         for (int th : threads)

@@ -1,20 +1,24 @@
 // awo_simulate.cu -- Monte-Carlo avalanche trajectories (Sec. 5.2).
 //
 // Design (GB300):
-//  * Persistent kernel, one lane per particle.  A warp takes a few release
-//    cells at a time from a global counter (one atomic per cell group) and
-//    walks their particles (cell-major, particle j minor) with a warp-uniform
-//    cursor; a lane is refilled the moment its particle ends, so lanes never
-//    idle behind a long particle of the same warp.  The particles in flight
-//    come from a compact window of the release list, so the lanes of a warp,
-//    and the warps of the GPU, touch a compact region of the DEM and of the
-//    rasters, which stays L2-resident even when the DEM does not.
-//  * No integer division on the refill path: the cursor carries (cell, j),
-//    and a cell index becomes (x, y) through a float reciprocal of W and one
-//    exact correction step.
-//  * A particle starts at refill time: the 2x2 footprint of its release cell
-//    is gathered and its release visit recorded (merged over the particles of
-//    the cell that start together).  Each loop iteration is then exactly one
+//  * Persistent kernel, one lane per particle.  The particles are numbered
+//    cell-major (release-list entry, then particle j); a warp takes a chunk
+//    of consecutive particles at a time from a global counter (one atomic per
+//    chunk) and walks it with a warp-uniform cursor; a lane is refilled the
+//    moment its particle ends, so lanes never idle behind a long particle of
+//    the same warp.  The chunk size (32 .. 1024 particles) follows from the
+//    particle count and the grid, so that a release list of a few cells is
+//    still spread over many warps.  The particles in flight come from a
+//    compact window of the release list, so the lanes of a warp, and the
+//    warps of the GPU, touch a compact region of the DEM and of the rasters,
+//    which stays L2-resident even when the DEM does not.
+//  * One integer division per chunk and none per particle: the cursor
+//    carries (cell, j), and a cell index becomes (x, y) through a float
+//    reciprocal of W and one exact correction step.
+//  * A particle starts at refill time from the 16-byte start record of its
+//    release cell (position, height, first direction), written by a prologue
+//    kernel that also records the release visits of all N particles of the
+//    cell with one reduction.  Each loop iteration is then exactly one
 //    move and its visit -- direction from the footprint kept in registers,
 //    draw, step, footprint and energy at the new position, record -- written
 //    without data-dependent branches (selects and predicated reductions), so
@@ -34,7 +38,7 @@
 namespace awo {
 
 struct SimWorkspace {
-    unsigned long long next_cell;  // global work counter, in release-list entries
+    unsigned long long next_item;  // global work counter, in particles
     unsigned long long stats[6];   // total_steps, n_traj, n_exited, n_capped, n_stopped, n_rejected
     unsigned long long pad;
 };
@@ -57,13 +61,13 @@ struct SimArgs {
     uint32_t n_cells_max;
     uint32_t n_grid;       // W*H
     uint32_t N;
-    uint32_t cells_per_fetch;
     SimWorkspace* ws;
     CellStart* starts;     // one per release-list entry
 };
 
 constexpr int SIM_THREADS = 128;
-constexpr uint32_t SIM_FETCH_ITEMS = 1024;  // particles per global fetch, at least
+constexpr uint32_t SIM_CHUNK_MAX = 1024;  // particles per global fetch, at most
+constexpr uint32_t SIM_CHUNKS_PER_WARP = 4;  // fetches a warp makes on an even split, at least
 
 __device__ __forceinline__ uint32_t release_count(const SimArgs& a)
 {
@@ -92,10 +96,18 @@ __global__ void __launch_bounds__(SIM_THREADS) k_simulate(const __grid_constant_
     const unsigned lane_lt = (1u << lane) - 1u;
     const uint32_t n_cells = release_count(a);
 
-    // warp-uniform cursor over (release-list entry, particle) and the end of
-    // the current cell group
-    uint32_t cur_ci = 0, cur_j = 0, end_ci = 0;
-    bool exhausted = (n_cells == 0u);
+    // particles in all, and the chunk a warp takes per fetch: a multiple of
+    // 32 in [32, SIM_CHUNK_MAX], about total / (warps * SIM_CHUNKS_PER_WARP)
+    const unsigned long long total = (unsigned long long)n_cells * a.N;
+    const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    unsigned long long chunk = total / (warps * SIM_CHUNKS_PER_WARP);
+    chunk = chunk < 32ull ? 32ull : (chunk > SIM_CHUNK_MAX ? (unsigned long long)SIM_CHUNK_MAX : chunk);
+    chunk &= ~31ull;
+
+    // warp-uniform cursor: next particle (t, and as (entry, j)) and the end of the chunk
+    unsigned long long cur_t = 0ull, end_t = 0ull;
+    uint32_t cur_ci = 0, cur_j = 0;
+    bool exhausted = (total == 0ull);
 
     AWO_LANE_STATE
 
@@ -103,18 +115,21 @@ __global__ void __launch_bounds__(SIM_THREADS) k_simulate(const __grid_constant_
         // ---- refill idle lanes (one round per move) ------------------------
         const unsigned idle = __ballot_sync(0xffffffffu, !live);
         if (idle != 0u && !exhausted) {
-            if (cur_ci >= end_ci) {
+            if (cur_t >= end_t) {
                 unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(&a.ws->next_cell, (unsigned long long)a.cells_per_fetch);
+                if (lane == 0) base = atomicAdd(&a.ws->next_item, chunk);
                 base = __shfl_sync(0xffffffffu, base, 0);
-                exhausted = base >= n_cells;
-                cur_ci = (uint32_t)min(base, (unsigned long long)n_cells);
-                cur_j = 0;
-                end_ci = (uint32_t)min((unsigned long long)n_cells, base + a.cells_per_fetch);
+                exhausted = base >= total;
+                if (!exhausted) {
+                    cur_t = base;
+                    end_t = min(total, base + chunk);
+                    cur_ci = (uint32_t)(base / a.N);  // one division per chunk
+                    cur_j = (uint32_t)(base - (unsigned long long)cur_ci * a.N);
+                }
             }
             if (!exhausted) {
-                // particles left in the group (capped at 32)
-                const unsigned long long left = (unsigned long long)(end_ci - cur_ci) * a.N - cur_j;
+                // particles left in the chunk (capped at 32)
+                const unsigned long long left = end_t - cur_t;
                 const unsigned avail = left < 32ull ? (unsigned)left : 32u;
                 const unsigned want = (unsigned)__popc(idle);
                 const unsigned take = want < avail ? want : avail;
@@ -132,6 +147,7 @@ __global__ void __launch_bounds__(SIM_THREADS) k_simulate(const __grid_constant_
                 my_traj += cap0 ? 1u : 0u;
                 live = live || (ok && !cap0);
                 advance(cur_ci, cur_j, take, a.N);
+                cur_t += take;
             }
         }
         if (__ballot_sync(0xffffffffu, live) == 0u) {
@@ -208,7 +224,6 @@ extern "C" awo_status awo_simulate(const float* d_h, awo_grid g, const uint32_t*
     a.muD = p->mu * D;
     a.N = p->traj_per_cell;
     a.max_steps = p->max_steps;
-    a.cells_per_fetch = a.N >= SIM_FETCH_ITEMS ? 1u : (SIM_FETCH_ITEMS + a.N - 1u) / a.N;
     uint32_t k0 = (uint32_t)(p->seed & 0xffffffffu), k1 = (uint32_t)(p->seed >> 32);
     for (int r = 0; r < 10; ++r) {
         a.keys.k0[r] = k0;

@@ -88,7 +88,7 @@ def test_every_tuning_gives_the_same_rasters():
     base_stats = b.stats_list()
     for rf in (awo.REFILL_LANE, awo.REFILL_WARP):
         for th in (64, 128, 256):
-            for gp in (32, 256, 1024, 4096):
+            for gp in (0, 32, 100, 256, 1024, 4096):
                 b.tuning = awo.Tuning(th, gp, rf, 0)
                 b.run()
                 torch.cuda.synchronize()

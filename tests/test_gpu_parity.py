@@ -298,6 +298,25 @@ def test_simulate_parameter_cases(kw):
         assert gs[k] == st[k], k
 
 
+@pytest.mark.parametrize("n_cells,N", [(1, 1000), (3, 2048), (2, 37), (5000, 1), (700, 3)])
+def test_simulate_chunking(n_cells, N):
+    """Work is handed out in chunks of particles that may split a release
+    cell or span many: a few cells with many particles, and many cells with
+    one or three particles, give the oracle's rasters bit for bit."""
+    z = inputs.fbm(96, 0.8, seed=21, relief=900.0, m=131).astype(np.float32)
+    H, W = z.shape
+    rng = np.random.default_rng(n_cells * 7 + N)
+    cells = np.sort(rng.choice(W * H, n_cells, replace=False)).astype(np.uint32)
+    op = _oparams(traj_per_cell=N, max_steps=400)
+    ov = _sim_pair(z, 10.0, cells, op)
+    c64, maxe, st = oracle.simulate(z, 10.0, cells, op)
+    assert np.array_equal(ov.count.cpu().numpy().view(np.uint32), oracle.counts_u32(c64))
+    assert np.array_equal(ov.maxe.cpu().numpy(), maxe)
+    gs = ov.stats_dict()
+    for k in st:
+        assert gs[k] == st[k], k
+
+
 @pytest.mark.parametrize("shape", [(1, 1), (2, 2), (1, 40), (40, 1), (3, 5)])
 def test_simulate_tiny_grids(shape):
     H, W = shape
