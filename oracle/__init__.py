@@ -36,7 +36,7 @@ def _params_type(precision: str):
         _fields_ = [("mu", creal), ("drag_k", creal), ("persistence", creal),
                     ("randomness", creal), ("step_scale", creal), ("gravity", creal),
                     ("traj_per_cell", ctypes.c_uint32), ("max_steps", ctypes.c_uint32),
-                    ("seed", ctypes.c_uint64)]
+                    ("seed", ctypes.c_uint64), ("release_log2", ctypes.c_int32)]
     return Params
 
 
@@ -148,6 +148,32 @@ def release(tan2: np.ndarray, lo_deg: float, hi_deg: float, precision: str = "f3
     return mask, cells[: n.value].copy()
 
 
+def release_texture_dims(W: int, H: int, r: int) -> tuple[int, int]:
+    """(Wr, Hr) of the release texture at 2^r times the DEM's resolution."""
+    wr, hr = ctypes.c_int64(0), ctypes.c_int64(0)
+    rc = lib("f32").orc_release_texture_dims(ctypes.c_int32(W), ctypes.c_int32(H), ctypes.c_int32(r),
+                                             ctypes.byref(wr), ctypes.byref(hr))
+    _check(rc, "orc_release_texture_dims")
+    return int(wr.value), int(hr.value)
+
+
+def release_texture(tan2: np.ndarray, r: int, lo_deg: float, hi_deg: float, precision: str = "f32"):
+    """Release points on the texture at 2^r times the DEM's resolution:
+    (mask[Hr, Wr] uint8, texel indices uint32 sorted)."""
+    _, npr = _real(precision)
+    t2 = np.ascontiguousarray(tan2, dtype=npr)
+    H, W = t2.shape
+    wr, hr = release_texture_dims(W, H, r)
+    mask = np.empty((hr, wr), dtype=np.uint8)
+    texels = np.empty(wr * hr, dtype=np.uint32)
+    n = ctypes.c_uint32(0)
+    rc = lib(precision).orc_release_texture(_ptr(t2), ctypes.c_int32(W), ctypes.c_int32(H), ctypes.c_int32(r),
+                                            ctypes.c_double(lo_deg), ctypes.c_double(hi_deg),
+                                            _ptr(mask), _ptr(texels), ctypes.byref(n))
+    _check(rc, "orc_release_texture")
+    return mask, texels[: n.value].copy()
+
+
 @dataclass
 class SimParams:
     mu: float = 0.46630765815499864  # tan(25 deg)
@@ -159,11 +185,12 @@ class SimParams:
     traj_per_cell: int = 16
     max_steps: int = 1000
     seed: int = 0
+    release_log2: int = 0  # list entries are texels of the release texture at 2^r x the DEM resolution
 
     def to_c(self, precision: str):
         return _PARAMS[precision](self.mu, self.drag_k, self.persistence, self.randomness,
                                   self.step_scale, self.gravity, self.traj_per_cell,
-                                  self.max_steps, self.seed)
+                                  self.max_steps, self.seed, self.release_log2)
 
 
 def simulate(h: np.ndarray, cs: float, cells: np.ndarray, params: SimParams,

@@ -97,6 +97,8 @@ typedef struct {
     uint32_t traj_per_cell;
     uint32_t max_steps;
     uint64_t seed;
+    int32_t release_log2; /* release texture at 2^r x the DEM resolution;   */
+                          /* 0: release-list entries are DEM cells           */
 } orc_params;
 
 typedef struct {
@@ -194,6 +196,55 @@ int orc_release(const real* tan2, int32_t W, int32_t H, double lo_deg, double hi
 }
 
 /* ------------------------------------------------------------------ */
+/* b''. Release points on a texture of chosen resolution (Sec. 5.2: the */
+/* user picks the texture resolution at which potential release points */
+/* are evaluated).  The texture covers the DEM's extent at 2^r times    */
+/* its resolution, r in [-3, 3]: Wr = W 2^r, Hr = H 2^r for r >= 0, and */
+/* the ceilings of W 2^r, H 2^r for r < 0 (the last texel then reaches  */
+/* past the DEM).  Texel (a, b) has its centre at                        */
+/*   u = (a + 1/2) 2^-r - 1/2,  v = (b + 1/2) 2^-r - 1/2                 */
+/* in cell units, clamped to the sampling domain [0, W-1] x [0, H-1]     */
+/* (exact in FP32: a few fraction bits, magnitude below 2^17).  The     */
+/* steepness there is the bilinear interpolation of the cells' tan^2,  */
+/* with the footprint and weights of the height sampling below; a texel */
+/* is a release point iff T_lo <= tan^2 <= T_hi.  At r = 0 the centres  */
+/* are the cell centres, the weights are 1 and 0, and the result is     */
+/* orc_release's.  Release-list entries are texel indices b Wr + a.     */
+/* ------------------------------------------------------------------ */
+#define ORC_RELEASE_LOG2_MAX 3
+
+int orc_release_texture_dims(int32_t W, int32_t H, int32_t r, int64_t* Wr, int64_t* Hr)
+{
+    if (W <= 0 || H <= 0 || r < -ORC_RELEASE_LOG2_MAX || r > ORC_RELEASE_LOG2_MAX) return ORC_EINVAL;
+    if (r >= 0) {
+        *Wr = (int64_t)W << r;
+        *Hr = (int64_t)H << r;
+    } else {
+        const int64_t q = (int64_t)1 << (-r);
+        *Wr = ((int64_t)W + q - 1) / q;
+        *Hr = ((int64_t)H + q - 1) / q;
+    }
+    if (*Wr * *Hr >= ((int64_t)1 << 31)) return ORC_EINVAL;
+    return ORC_OK;
+}
+
+static real texel_axis(int64_t a, int32_t r, int32_t n)
+{
+    double c = ldexp((double)a + 0.5, -r) - 0.5;
+    if (c < 0.0) c = 0.0;
+    if (c > (double)(n - 1)) c = (double)(n - 1);
+    return (real)c;
+}
+
+/* Start position of release-list entry t (a texel index of the release */
+/* texture at 2^r; a cell index at r = 0).                              */
+static void release_point(int32_t W, int32_t H, int32_t r, int64_t Wr, uint32_t t, real* u, real* v)
+{
+    *u = texel_axis((int64_t)t % Wr, r, W);
+    *v = texel_axis((int64_t)t / Wr, r, H);
+}
+
+/* ------------------------------------------------------------------ */
 /* Bilinear sampling of the DEM.  Positions are in cell units: cell   */
 /* (x, y) has its centre at (u, v) = (x, y); the sampling domain is    */
 /* u in [0, W-1], v in [0, H-1].                                       */
@@ -227,6 +278,30 @@ static real bilinear_height(const footprint* f)
     real top = f->h00 * ox + f->h10 * f->fx;
     real bot = f->h01 * ox + f->h11 * f->fx;
     return top * oy + bot * f->fy;
+}
+
+int orc_release_texture(const real* tan2, int32_t W, int32_t H, int32_t r, double lo_deg, double hi_deg,
+                        uint8_t* mask, uint32_t* texels, uint32_t* n_out)
+{
+    int64_t Wr, Hr;
+    if (orc_release_texture_dims(W, H, r, &Wr, &Hr)) return ORC_EINVAL;
+    if (!(lo_deg >= 0.0) || !(hi_deg < 90.0) || lo_deg > hi_deg) return ORC_EINVAL;
+    real t_lo = tan2_of_degrees(lo_deg), t_hi = tan2_of_degrees(hi_deg);
+    uint32_t n = 0;
+    for (int64_t t = 0; t < Wr * Hr; ++t) {
+        real u, v;
+        release_point(W, H, r, Wr, (uint32_t)t, &u, &v);
+        footprint f = take_footprint(tan2, W, H, u, v);
+        real T = bilinear_height(&f);
+        int sel = (t_lo <= T) && (T <= t_hi);
+        if (mask) mask[t] = (uint8_t)sel;
+        if (sel) {
+            if (texels) texels[n] = (uint32_t)t;
+            ++n;
+        }
+    }
+    *n_out = n;
+    return ORC_OK;
 }
 
 /* Steepest-descent unit direction of the bilinear patch (Sec. 5.2:    */
@@ -301,8 +376,10 @@ void orc_draw(uint32_t cell, uint32_t j, uint32_t n, uint64_t seed, real xi[2])
 /* State: position p = (u, v) in cells, unit direction d, energy-line  */
 /* height e in metres (kinetic energy per unit weight, v^2 / 2g), and  */
 /* the sampled height z at p.                                           */
-/*   start: p0 = release cell centre, e0 = 0, d0 = g(p0) (zero if flat);*/
-/*          the start is a visit of the release cell with e = 0.         */
+/*   start: p0 = release cell centre (or release texel centre), e0 = 0, */
+/*          d0 = g(p0) (zero if flat); the start is a visit of the cell  */
+/*          of p0 with e = 0.  The random stream is keyed by the list    */
+/*          entry (cell or texel index).                                 */
 /*   move n = 0, 1, ... while n < max_steps:                            */
 /*     g  = steepest-descent direction at p_n (fallback d_n)            */
 /*     xi = two uniforms in [-1,1) from Philox (cell, j, n)             */
@@ -329,8 +406,8 @@ typedef struct {
     int32_t end;     /* END_* */
 } orc_trace_buf;
 
-static int run_trajectory(const real* h, int32_t W, int32_t H, real cs, uint32_t cell, uint32_t j,
-                          const orc_params* p, uint64_t* count, real* maxe, orc_stats* st,
+static int run_trajectory(const real* h, int32_t W, int32_t H, real cs, uint32_t cell, real u0, real v0,
+                          uint32_t j, const orc_params* p, uint64_t* count, real* maxe, orc_stats* st,
                           orc_trace_buf* tr)
 {
     const real P = p->persistence, R = p->randomness, s = p->step_scale;
@@ -338,7 +415,7 @@ static int run_trajectory(const real* h, int32_t W, int32_t H, real cs, uint32_t
     const real D = s * cs;
     const real kD = p->drag_k * D, muD = p->mu * D;
 
-    real u = (real)(cell % (uint32_t)W), v = (real)(cell / (uint32_t)W);
+    real u = u0, v = v0;
     footprint f = take_footprint(h, W, H, u, v);
     real z = bilinear_height(&f);
     real e = 0;
@@ -416,21 +493,30 @@ static int check_params(int32_t W, int32_t H, real cs, const orc_params* p)
     if (!(p->step_scale > 0) || !(p->step_scale <= 1)) return ORC_EINVAL;
     if (!(p->gravity > 0)) return ORC_EINVAL;
     if (!(p->drag_k * (p->step_scale * cs) < (real)1)) return ORC_EINVAL;
+    int64_t Wr, Hr;
+    if (orc_release_texture_dims(W, H, p->release_log2, &Wr, &Hr)) return ORC_EINVAL;
     return ORC_OK;
 }
 
-/* Runs traj_per_cell trajectories from every listed release cell and   */
-/* accumulates visits into count (uint64, caller zero-fills) and maxe   */
-/* (caller zero-fills).  Stats are accumulated into *st.               */
+
+/* Runs traj_per_cell trajectories from every listed release cell (or   */
+/* texel, when p->release_log2 != 0) and accumulates visits into count  */
+/* (uint64, caller zero-fills) and maxe (caller zero-fills).  Stats are  */
+/* accumulated into *st.                                                */
 int orc_simulate(const real* h, int32_t W, int32_t H, real cs, const uint32_t* cells, uint32_t n_cells,
                  const orc_params* p, uint64_t* count, real* maxe, orc_stats* st)
 {
     int rc = check_params(W, H, cs, p);
     if (rc) return rc;
+    int64_t Wr, Hr;
+    orc_release_texture_dims(W, H, p->release_log2, &Wr, &Hr);
+    const int64_t n_entries = Wr * Hr;
     for (uint32_t c = 0; c < n_cells; ++c) {
-        if ((int64_t)cells[c] >= (int64_t)W * H) return ORC_EINVAL;
+        if ((int64_t)cells[c] >= n_entries) return ORC_EINVAL;
+        real u0, v0;
+        release_point(W, H, p->release_log2, Wr, cells[c], &u0, &v0);
         for (uint32_t j = 0; j < p->traj_per_cell; ++j)
-            run_trajectory(h, W, H, cs, cells[c], j, p, count, maxe, st, NULL);
+            run_trajectory(h, W, H, cs, cells[c], u0, v0, j, p, count, maxe, st, NULL);
     }
     return ORC_OK;
 }
@@ -442,9 +528,13 @@ int orc_trace(const real* h, int32_t W, int32_t H, real cs, uint32_t cell, uint3
 {
     int rc = check_params(W, H, cs, p);
     if (rc) return rc;
-    if ((int64_t)cell >= (int64_t)W * H) return ORC_EINVAL;
+    int64_t Wr, Hr;
+    orc_release_texture_dims(W, H, p->release_log2, &Wr, &Hr);
+    if ((int64_t)cell >= Wr * Hr) return ORC_EINVAL;
+    real u0, v0;
+    release_point(W, H, p->release_log2, Wr, cell, &u0, &v0);
     orc_trace_buf tr = {cap, 0, u, v, e, cells, 0};
-    run_trajectory(h, W, H, cs, cell, j, p, NULL, NULL, NULL, &tr);
+    run_trajectory(h, W, H, cs, cell, u0, v0, j, p, NULL, NULL, NULL, &tr);
     *n_out = tr.n;
     *end_out = tr.end;
     return ORC_OK;
@@ -549,7 +639,7 @@ int orc_soft_forward(const real* h, int32_t W, int32_t H, real cs, const uint32_
 {
     int rc = check_params(W, H, cs, p);
     if (rc) return rc;
-    if (!(tau > 0)) return ORC_EINVAL;
+    if (!(tau > 0) || p->release_log2 != 0) return ORC_EINVAL; /* soft mode: DEM cells only */
     soft_path sp;
     if (soft_path_alloc(&sp, p->max_steps)) return ORC_ENOMEM;
     for (uint32_t c = 0; c < n_cells; ++c) {
@@ -584,7 +674,7 @@ int orc_soft_gradient(const real* h, int32_t W, int32_t H, real cs, const uint32
 {
     int rc = check_params(W, H, cs, p);
     if (rc) return rc;
-    if (!(tau > 0)) return ORC_EINVAL;
+    if (!(tau > 0) || p->release_log2 != 0) return ORC_EINVAL; /* soft mode: DEM cells only */
     soft_path sp;
     if (soft_path_alloc(&sp, p->max_steps)) return ORC_ENOMEM;
     const double D = (double)(p->step_scale * cs);

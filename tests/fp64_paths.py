@@ -74,15 +74,20 @@ def _cell(W, cs, X, Y, mg):
 
 
 def path(h, cs, cell, j, *, mu, drag_k=0.0, persistence=0.9, randomness=0.16,
-         step_scale=1.0, max_steps=64, seed=0):
-    """Returns dict(X, Y, e, cell, end, margin) for trajectory (cell, j)."""
+         step_scale=1.0, max_steps=64, seed=0, start=None):
+    """Returns dict(X, Y, e, cell, end, margin) for trajectory (cell, j).
+    ``cell`` keys the random stream; the start is the centre of that cell
+    unless ``start`` gives it in metres (a release texel's centre)."""
     h = np.asarray(h, dtype=np.float64)
     H, W = h.shape
     mg = Margin()
     P, R = persistence, randomness
     D = step_scale * cs
-    X = (cell % W + 0.5) * cs
-    Y = (cell // W + 0.5) * cs
+    if start is None:
+        X = (cell % W + 0.5) * cs
+        Y = (cell // W + 0.5) * cs
+    else:
+        X, Y = float(start[0]), float(start[1])
     z, gx, gy = _sample(h, cs, X, Y, None)
     nrm = math.hypot(gx, gy)
     dx, dy = (-gx / nrm, -gy / nrm) if nrm > 0 else (0.0, 0.0)
