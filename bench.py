@@ -53,7 +53,7 @@ ALG_OPS_PER_VISIT = 176
 # read + write of a 6144^2 crop launch, divided by its visits), keyed by the
 # SHA-256 prefix of the kernel source it was taken on; a changed kernel
 # reports traffic null until it is captured again.
-DRAM_BYTES_PER_VISIT: dict[str, float] = {"0623e1604391b370": (267.430656e6 + 54.800128e6) / 1754008332}
+DRAM_BYTES_PER_VISIT: dict[str, float] = {"3ceb0b2590210628": (267.34336e6 + 54.842112e6) / 1754008332}
 
 
 def _args():
@@ -70,6 +70,8 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--release-log2", type=int, default=0,
+                    help="evaluate release points on a texture at 2^r x the DEM resolution (large/mid/tiny)")
     return ap.parse_args()
 
 
@@ -201,8 +203,12 @@ def _peaks() -> dict:
 
 
 def _kernel_sha() -> str:
-    p = os.path.join(ROOT, "paper_2506_23364_gb300", "csrc", "awo_simulate.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    """Hash of the particle kernel's sources (the kernel and its per-move code)."""
+    h = hashlib.sha256()
+    for name in ("awo_simulate.cu", "awo_particle.cuh"):
+        with open(os.path.join(ROOT, "paper_2506_23364_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def _probe_peaks(torch, awo) -> dict:
@@ -285,7 +291,7 @@ def run_awo(args, R: Ranks):
                                 step_scale=w.step_scale, gravity=w.gravity, traj_per_cell=w.traj_per_cell,
                                 max_steps=w.max_steps, seed=w.seed)
     ov = awo.Overlay(w.width, w.height, w.cell_size, quantised=w.quantised, levels=w.lod_levels,
-                     device=R.device, want_slope=False)
+                     device=R.device, want_slope=False, release_log2=args.release_log2)
     host_dem = w.dem_u16 if w.quantised else w.dem_f32
     ov.load_dem(host_dem)
     torch.cuda.synchronize()
@@ -330,30 +336,8 @@ def run_awo(args, R: Ranks):
     value = total_steps_all / (ms_step_max / 1e3)
 
     # end to end through the API with host buffers: H2D of the DEM, D2H of the overlay (all levels)
-    pin_dem = torch.from_numpy(np.ascontiguousarray(host_dem).view(np.int16) if w.quantised else host_dem).pin_memory()
-    outs = [(ov.count, torch.empty(ov.count.shape, dtype=torch.int32).pin_memory()),
-            (ov.vel, torch.empty(ov.vel.shape, dtype=torch.float32).pin_memory())]
-    for c, v in zip(ov.count_lv, ov.vel_lv):
-        outs.append((c, torch.empty(c.shape, dtype=torch.int32).pin_memory()))
-        outs.append((v, torch.empty(v.shape, dtype=torch.float32).pin_memory()))
-    bi = pin_dem.numel() * pin_dem.element_size()
-    bo = sum(h.numel() * h.element_size() for _, h in outs)
-    dst = ov.q if w.quantised else ov.h
-    e2e_ms = []
-    for k in range(max(args.e2e_steps, 1) + 1):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        R.barrier()
-        a.record()
-        dst.copy_(pin_dem, non_blocking=True)
-        step()
-        for d, h in outs:
-            h.copy_(d, non_blocking=True)
-        b.record()
-        b.synchronize()
-        if k > 0:
-            e2e_ms.append(a.elapsed_time(b))
-    e2e_step = R.reduce(statistics.mean(e2e_ms), "max")
-    e2e_value = total_steps_all / (e2e_step / 1e3)
+    e2e = _e2e(args, R, awo, w, ov, host_dem, lambda o: (o.terrain(lo, hi), o.simulate(params), o.overlay(w.gravity)),
+               float(st["total_steps"]), total_steps_all)
 
     peaks = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
@@ -386,19 +370,89 @@ def run_awo(args, R: Ranks):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded fBm + carved valleys, uint16 dm)",
             "config": dict(w.describe(), parallelism=f"replicas x{R.world}" if R.world > 1 else "single GPU",
                            l2="inputs larger than L2 (uint16 DEM 128 MiB + FP32 DEM 256 MiB + rasters)",
-                           release_cells=ov.n_release()),
+                           release_cells=ov.n_release(), **({"release_texture_log2": args.release_log2,
+                                                             "release_texture": [ov.g_rel.width, ov.g_rel.height]}
+                                                            if args.release_log2 else {})),
             "ms_per_overlay": ms_step_max, "simulate_ms": sim_ms,
             "simulate_steps_per_s": st["total_steps"] / (sim_ms / 1e3),
             "particles_per_s": st["n_traj"] / (sim_ms / 1e3), "stats": st,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
-                    "ms_per_step": e2e_step},
+            "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "roofline": roofline, "roofline_l2": l2,
             "roofline_hbm": roofline_hbm,
             "clocks": clk, "kernel_sha": sha}
-    if R.rank == 0 and R.world == 1 and not args.no_cpu_baseline:
+    if R.rank == 0 and R.world == 1 and not args.no_cpu_baseline and not args.release_log2:
         line["cpu_baseline"] = _cpu_baseline(w, args.cpu_seconds)
     if R.rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def _e2e(args, R, awo, w, ov, host_dem, run, steps_one, steps_all) -> dict:
+    """The same workload end to end through the public API: every step copies
+    its DEM from pinned host memory, runs the workflow and copies the whole
+    overlay (count and velocity, every mipmap level) back to pinned host
+    memory.  Pipelined form (the value): two workflow instances on two CUDA
+    streams take steps in turn, so the copies of one step overlap the kernels
+    of the next.  Serial form (reported beside it): one stream, each step
+    synchronised before the next."""
+    import numpy as np
+    import torch
+
+    src = np.ascontiguousarray(host_dem).view(np.int16) if w.quantised else host_dem
+    pin_dem = torch.from_numpy(src).pin_memory()
+    ov2 = awo.Overlay(w.width, w.height, w.cell_size, quantised=w.quantised, levels=w.lod_levels,
+                      device=R.device, want_slope=False, release_log2=ov.release_log2)
+
+    def outs_of(o):
+        dev = [o.count, o.vel] + [t for pair in zip(o.count_lv, o.vel_lv) for t in pair]
+        return [(d, torch.empty(d.shape, dtype=d.dtype).pin_memory()) for d in dev]
+
+    insts = [(ov, outs_of(ov), torch.cuda.Stream(R.device)), (ov2, outs_of(ov2), torch.cuda.Stream(R.device))]
+    bi = pin_dem.numel() * pin_dem.element_size()
+    bo = sum(h.numel() * h.element_size() for _, h in insts[0][1])
+
+    def one(inst):
+        o, outs, s = inst
+        with torch.cuda.stream(s):
+            (o.q if w.quantised else o.h).copy_(pin_dem, non_blocking=True)
+            run(o)
+            for d, h in outs:
+                h.copy_(d, non_blocking=True)
+
+    n = max(args.e2e_steps, 1)
+    # serial: one instance, synchronised per step
+    serial = []
+    for k in range(n + 1):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        R.barrier()
+        a.record(insts[0][2])
+        one(insts[0])
+        b.record(insts[0][2])
+        b.synchronize()
+        if k > 0:
+            serial.append(a.elapsed_time(b))
+    serial_ms = R.reduce(statistics.mean(serial), "max")
+    # pipelined: 2 instances on 2 streams, 2 * n steps after 2 warm-up steps
+    for inst in insts:
+        one(inst)
+    torch.cuda.synchronize()
+    R.barrier()
+    s0, s1 = insts[0][2], insts[1][2]
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s0)
+    s1.wait_event(a)
+    k_steps = 2 * n
+    for k in range(k_steps):
+        one(insts[k % 2])
+    s0.wait_stream(s1)
+    b.record(s0)
+    b.synchronize()
+    pipe_ms = R.reduce(a.elapsed_time(b) / k_steps, "max")
+    del ov2
+    return {"value": steps_all / (pipe_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": bi,
+            "d2h_bytes_per_step": bo, "ms_per_step": pipe_ms, "steps": k_steps,
+            "form": "2 workflow instances on 2 CUDA streams, steps alternate (copies overlap the next step)",
+            "serial": {"value": steps_all / (serial_ms / 1e3), "ms_per_step": serial_ms, "steps": n,
+                       "form": "1 stream, synchronised after every step"}}
 
 
 def _region_params(awo, r):

@@ -65,7 +65,9 @@ typedef struct {
     uint32_t max_steps;   /* moves per particle at most                               */
     uint64_t seed;        /* Philox key (low word, high word)                         */
     uint32_t flags;       /* AWO_SIM_* bits below; 0 = accumulate                     */
-    uint32_t reserved;    /* 0                                                        */
+    int32_t release_log2; /* r in [-3, 3]: the release list holds texels of the release */
+                          /* texture at 2^r x the DEM resolution (awo_release_texture); */
+                          /* 0: the list holds DEM cells                               */
 } awo_sim_params;
 
 /* awo_sim_params.flags: clear d_count and d_maxe (cudaMemsetAsync on the
@@ -79,7 +81,7 @@ typedef struct {
     uint64_t n_exited;    /* left the sampling domain                        */
     uint64_t n_capped;    /* reached max_steps                               */
     uint64_t n_stopped;   /* energy reached zero (or zero direction)         */
-    uint64_t n_rejected;  /* particles skipped: release index >= W*H         */
+    uint64_t n_rejected;  /* particles skipped: release index >= W*H (Wr*Hr) */
 } awo_sim_stats;
 
 const char* awo_status_string(awo_status s);
@@ -136,6 +138,35 @@ awo_status awo_release_from_mask(const uint8_t* d_mask, awo_grid g, uint32_t* d_
                                  void* d_ws, size_t ws_bytes, void* stream);
 
 /*
+ * b''. Release points on a texture of chosen resolution (Sec. 5.2: the user
+ * chooses the texture resolution at which potential release points are
+ * evaluated).  The release texture covers the DEM's extent at 2^r times its
+ * resolution, r = release_log2 in [-AWO_RELEASE_LOG2_MAX, AWO_RELEASE_LOG2_MAX]:
+ * Wr x Hr = (W 2^r) x (H 2^r) for r >= 0, ceil(W 2^r) x ceil(H 2^r) for r < 0
+ * (awo_release_texture_dims; Wr * Hr < 2^31).  Exact.  Texel (a, b) has its
+ * centre at
+ *   u = (a + 1/2) 2^-r - 1/2,  v = (b + 1/2) 2^-r - 1/2   (cell units: cell
+ *   (x, y) is centred at (x, y)), each clamped to [0, W-1] resp. [0, H-1]
+ * (exact in FP32).  Its steepness T is the bilinear interpolation of d_tan2
+ * with the footprint and weights of the particle's height sampling (see
+ * awo_simulate); the texel is a release point iff T_lo <= T <= T_hi, the
+ * bounds as in awo_release.  At r = 0 this is awo_release.
+ * Outputs: d_mask uint8 [Hr*Wr] (0/1, required); d_texels uint32 [capacity
+ * Hr*Wr]: texel indices b*Wr + a in increasing order; d_n: their number.
+ * A caller's mask at the texture's resolution (known release points) goes
+ * through awo_release_from_mask with the grid {Wr, Hr, cell_size 2^-r}.
+ * Run the particles with awo_sim_params.release_log2 = r.
+ * Workspace: awo_release_texture_workspace_bytes(g, r) bytes, 16-byte
+ * aligned, contents undefined on entry and exit.
+ */
+#define AWO_RELEASE_LOG2_MAX 3
+awo_status awo_release_texture_dims(awo_grid g, int32_t release_log2, int32_t* width, int32_t* height);
+size_t awo_release_texture_workspace_bytes(awo_grid g, int32_t release_log2);
+awo_status awo_release_texture(const float* d_tan2, awo_grid g, int32_t release_log2, double slope_lo_deg,
+                               double slope_hi_deg, uint8_t* d_mask, uint32_t* d_texels, uint32_t* d_n,
+                               void* d_ws, size_t ws_bytes, void* stream);
+
+/*
  * Release selection without a caller-provided workspace.  (The paper has no
  * counterpart: this is a library convenience.)  Some callers cannot hand the
  * library any extra device memory: a plug-in inside a host application, such
@@ -166,7 +197,10 @@ awo_status awo_release_noalloc(const float* d_tan2, awo_grid g, double slope_lo_
  * zero-fill both before the first call, or set AWO_SIM_CLEAR_OUTPUTS).
  * Particle (cell c, j):
  *   start: p = centre of c, e = 0, d = g(p) (zero vector on flat ground);
- *          the start is a visit of c with e = 0.
+ *          the start is a visit of c with e = 0.  With release_log2 = r != 0
+ *          the list entry c is a texel of the release texture (see
+ *          awo_release_texture), p is that texel's centre, and the start is a
+ *          visit of the cell of p (rule below); the random counter keeps c.
  *   move n = 0, 1, ... while n < max_steps:
  *     footprint of p: i0 = floor(u), j0 = floor(v), fx = u - i0, fy = v - j0,
  *       i1 = min(i0+1, W-1), j1 = min(j0+1, H-1); heights h00 = h[j0][i0],
@@ -186,8 +220,9 @@ awo_status awo_release_noalloc(const float* d_tan2, awo_grid g, double slope_lo_
  *   visit(cell, e): count += 1; maxe = max(maxe, e)
  * With drag_k = 0, e is the energy-line height: e_n = z_0 - z_n - mu * (path
  * length), and stopping at e <= 0 is the runout-angle criterion.
- * d_h: float [H*W].  d_cells: uint32 cell indices (< H*W; a larger index
- * is skipped on the device and counted in n_rejected).  The number of
+ * d_h: float [H*W].  d_cells: uint32 cell indices (< H*W; texel indices
+ * < Wr*Hr when release_log2 != 0; a larger index is skipped on the device
+ * and counted in n_rejected).  The number of
  * release cells is min(*d_n_cells, n_cells_max) when d_n_cells is non-null
  * (read on the device, so no host sync is needed after awo_release), else
  * n_cells_max.  d_count: uint32 [H*W], wraps modulo 2^32 (the call is
@@ -195,8 +230,8 @@ awo_status awo_release_noalloc(const float* d_tan2, awo_grid g, double slope_lo_
  * d_maxe: float [H*W], non-negative (metres of energy-line height).
  * d_stats: awo_sim_stats on the device, overwritten (nullable).
  * Workspace: at least awo_simulate_workspace_bytes(n_cells_max) bytes,
- * 16-byte aligned (a work counter, the statistics, and a 16-byte start
- * record per release cell); contents undefined on entry and exit.
+ * 16-byte aligned (a work counter, the statistics, and a start record of up
+ * to 32 bytes per release-list entry); contents undefined on entry and exit.
  */
 size_t awo_simulate_workspace_bytes(uint32_t n_cells_max);
 awo_status awo_simulate(const float* d_h, awo_grid g, const uint32_t* d_cells,
@@ -299,7 +334,7 @@ awo_status awo_tune_batched(const awo_sim_request* reqs, int32_t n_req, void* d_
  * step.  Sums over particles are FP64.
  * Both take a workspace of awo_soft_workspace_bytes(n_cells_max) bytes.
  * tau > 0 in metres of energy-line height (1 m in the differentiable
- * workload).
+ * workload).  The release list holds DEM cells: release_log2 must be 0.
  */
 size_t awo_soft_workspace_bytes(uint32_t n_cells_max);
 awo_status awo_soft_forward(const float* d_h, awo_grid g, const uint32_t* d_cells, const uint32_t* d_n_cells,

@@ -47,13 +47,13 @@ class SimParams(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_float), ("drag_k", ctypes.c_float), ("persistence", ctypes.c_float),
                 ("randomness", ctypes.c_float), ("step_scale", ctypes.c_float), ("gravity", ctypes.c_float),
                 ("traj_per_cell", ctypes.c_uint32), ("max_steps", ctypes.c_uint32), ("seed", ctypes.c_uint64),
-                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("release_log2", ctypes.c_int32)]
 
     @classmethod
     def make(cls, mu=math.tan(math.radians(25.0)), drag_k=0.0, persistence=0.9, randomness=0.16,
-             step_scale=1.0, gravity=9.81, traj_per_cell=16, max_steps=1000, seed=0, flags=0):
+             step_scale=1.0, gravity=9.81, traj_per_cell=16, max_steps=1000, seed=0, flags=0, release_log2=0):
         return cls(mu, drag_k, persistence, randomness, step_scale, gravity, traj_per_cell, max_steps,
-                   seed, flags, 0)
+                   seed, flags, release_log2)
 
 
 class SimRequest(ctypes.Structure):
@@ -129,6 +129,9 @@ def lib() -> ctypes.CDLL:
         "awo_release": (st, [vp, Grid, f64, f64, vp, vp, vp, vp, sz, vp]),
         "awo_release_noalloc": (st, [vp, Grid, f64, f64, vp, vp, vp, vp]),
         "awo_release_from_mask": (st, [vp, Grid, vp, vp, vp, sz, vp]),
+        "awo_release_texture_dims": (st, [Grid, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "awo_release_texture_workspace_bytes": (sz, [Grid, i32]),
+        "awo_release_texture": (st, [vp, Grid, i32, f64, f64, vp, vp, vp, vp, sz, vp]),
         "awo_simulate_workspace_bytes": (sz, [u32]),
         "awo_simulate": (st, [vp, Grid, vp, vp, u32, ctypes.POINTER(SimParams), vp, vp, vp, vp, sz, vp]),
         "awo_finalize": (st, [vp, Grid, f32, vp, vp]),
@@ -232,6 +235,36 @@ def awo_release_from_mask(mask: torch.Tensor, g: Grid, cells: torch.Tensor, n: t
     _check(lib().awo_release_from_mask(_dev(mask, torch.uint8, c, "mask"), g, _dev(cells, cells.dtype, c, "cells"),
                                        _dev(n, n.dtype, 1, "n"), _dev(ws, torch.uint8, None, "ws"), ws.numel(),
                                        _stream(stream)), "awo_release_from_mask")
+
+
+RELEASE_LOG2_MAX = 3
+
+
+def awo_release_texture_dims(g: Grid, release_log2: int) -> tuple[int, int]:
+    """(Wr, Hr) of the release texture at 2^release_log2 times the DEM resolution."""
+    w, h = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(lib().awo_release_texture_dims(g, int(release_log2), ctypes.byref(w), ctypes.byref(h)),
+           "awo_release_texture_dims")
+    return int(w.value), int(h.value)
+
+
+def awo_release_texture_workspace_bytes(g: Grid, release_log2: int) -> int:
+    return int(lib().awo_release_texture_workspace_bytes(g, int(release_log2)))
+
+
+def awo_release_texture(tan2: torch.Tensor, g: Grid, release_log2: int, slope_lo_deg: float, slope_hi_deg: float,
+                        mask: torch.Tensor, texels: torch.Tensor, n: torch.Tensor, ws: torch.Tensor, stream=None):
+    """Release points on the texture at 2^release_log2 times the DEM resolution:
+    mask [Hr, Wr] uint8 and the ordered texel indices."""
+    wr, hr = awo_release_texture_dims(g, release_log2)
+    t = wr * hr
+    if texels.dtype not in (torch.int32, torch.uint32) or n.dtype not in (torch.int32, torch.uint32):
+        raise TypeError("texels and n must be int32 or uint32")
+    _check(lib().awo_release_texture(_dev(tan2, torch.float32, g.cells, "tan2"), g, int(release_log2),
+                                     slope_lo_deg, slope_hi_deg, _dev(mask, torch.uint8, t, "mask"),
+                                     _dev(texels, texels.dtype, t, "texels"), _dev(n, n.dtype, 1, "n"),
+                                     _dev(ws, torch.uint8, None, "ws"), ws.numel(), _stream(stream)),
+           "awo_release_texture")
 
 
 RELEASE_NOALLOC_MAX_CELLS = 8192 * 8192

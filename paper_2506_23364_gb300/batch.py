@@ -39,16 +39,17 @@ class Batch:
         for p in self.params:
             p.flags |= SIM_CLEAR_OUTPUTS
         self.ovs = []
-        for dem, cs, qz, lv in zip(dems, _per_region(cell_size, self.n), _per_region(quantised, self.n),
-                                   _per_region(levels, self.n)):
+        for dem, cs, qz, lv, p in zip(dems, _per_region(cell_size, self.n), _per_region(quantised, self.n),
+                                      _per_region(levels, self.n), self.params):
             H, W = dem.shape
-            ov = Overlay(W, H, cs, quantised=qz, levels=lv, device=device, want_normals=False, want_mask=False)
+            ov = Overlay(W, H, cs, quantised=qz, levels=lv, device=device, want_normals=False, want_mask=False,
+                         release_log2=p.release_log2)
             if load:
                 ov.load_dem(dem)
             self.ovs.append(ov)
         self.reqs = (SimRequest * self.n)()
         for i, ov in enumerate(self.ovs):
-            self.reqs[i] = sim_request(ov.h, ov.g, ov.cells, ov.n_rel, ov.g.cells, self.params[i], ov.count,
+            self.reqs[i] = sim_request(ov.h, ov.g, ov.cells, ov.n_rel, ov.n_tex, self.params[i], ov.count,
                                        ov.maxe)
         self.ws = torch.empty(awo_simulate_batched_workspace_bytes(self.reqs) + 256, dtype=torch.uint8,
                               device=device)

@@ -17,6 +17,8 @@
 //                    32 particles together (AWO_REFILL_WARP).
 // The per-move arithmetic is the one of awo_particle.cuh, so every request's
 // rasters equal those of awo_simulate on that request alone.
+#include <math.h>
+
 #include <algorithm>
 #include <cstddef>
 #include <cstring>
@@ -41,6 +43,8 @@ struct BatchReq {
     uint32_t n_cells_max, n_grid, N;
     uint32_t k0, k1;      // Philox key (seed words)
     uint32_t starts_off;  // index of this request's first start record
+    uint32_t texel;       // 1: the release list holds texels of the release texture
+    TexelGeom tg;
 };
 
 struct BatchHeader {
@@ -65,8 +69,9 @@ struct BatchArgs {
     uint32_t group;      // particles per chunk (0 = chosen by k_batch_prepare)
     uint32_t sim_warps;  // warps of the k_batch_simulate grid
     BatchHeader* hdr;
-    CellStart* starts;
+    TexelStart* starts;  // one 32-byte slot per release-list entry (a CellStart fills the first half)
 };
+static_assert(sizeof(BatchArgs) <= 32764, "the request table must fit the kernel parameter block");
 
 // Warp-register copy of the current request's constants.
 struct ReqRegs {
@@ -76,8 +81,9 @@ struct ReqRegs {
     int W, H;
     float Wm1, Hm1, P, oneP, R, s, kD, muD;
     uint32_t max_steps, N;
-    const CellStart* starts;
+    const TexelStart* starts;
     uint32_t k0, k1;
+    bool texel;
 };
 
 __device__ __forceinline__ ReqRegs load_req(const BatchArgs& a, int r)
@@ -102,6 +108,7 @@ __device__ __forceinline__ ReqRegs load_req(const BatchArgs& a, int r)
     q.starts = a.starts + b.starts_off;
     q.k0 = b.k0;
     q.k1 = b.k1;
+    q.texel = b.texel != 0u;
     return q;
 }
 
@@ -176,10 +183,16 @@ __global__ void __launch_bounds__(256) k_batch_starts(const __grid_constant__ Ba
         const int r = find_request<uint32_t>(s_cp, n, g);
         const BatchReq& q = a.r[r];
         const uint32_t ci = g - s_cp[r];
-        const uint32_t cell = __ldg(q.cells + ci);
-        const CellStart st = cell_start(q.h, q.W, q.H, q.n_grid, cell);
-        if (st.xy != ~0u) atomicAdd(q.count + cell, q.N);
-        a.starts[q.starts_off + ci] = st;
+        const uint32_t entry = __ldg(q.cells + ci);
+        if (q.texel) {
+            const TexelStart st = texel_start(q.h, q.W, q.H, q.tg, entry);
+            if (st.t != ~0u) atomicAdd(q.count + st.vcell, q.N);
+            a.starts[q.starts_off + ci] = st;
+        } else {
+            const CellStart st = cell_start(q.h, q.W, q.H, q.n_grid, entry);
+            if (st.xy != ~0u) atomicAdd(q.count + entry, q.N);
+            *reinterpret_cast<CellStart*>(a.starts + q.starts_off + ci) = st;
+        }
     }
 }
 
@@ -250,11 +263,15 @@ __global__ void __launch_bounds__(THREADS) k_batch_simulate(const __grid_constan
             const bool mine = ((idle >> lane) & 1u) && rank < take;
             uint32_t ci = cur_ci, jj = cur_j;
             advance(ci, jj, rank < take ? rank : 0u, q.N);
-            uint4 st = make_uint4(~0u, 0u, 0u, 0u);
-            if (mine) st = __ldg(reinterpret_cast<const uint4*>(q.starts) + ci);
+            uint4 st = make_uint4(~0u, 0u, 0u, 0u), st1 = make_uint4(0u, 0u, 0u, 0u);
+            if (mine) st = __ldg(reinterpret_cast<const uint4*>(q.starts) + 2u * ci);
+            if (mine && q.texel) st1 = __ldg(reinterpret_cast<const uint4*>(q.starts) + 2u * ci + 1u);
             const bool ok = mine && st.x != ~0u;
             my_bad += (mine && !ok) ? 1u : 0u;
-            AWO_LANE_START(ok, st, jj, q.W);
+            if (q.texel)  // warp-uniform
+                AWO_LANE_START_TEXEL(ok, st, st1, jj);
+            else
+                AWO_LANE_START(ok, st, jj, q.W);
             const bool cap0 = ok && q.max_steps == 0u;
             my_cap += cap0 ? 1u : 0u;
             my_traj += cap0 ? 1u : 0u;
@@ -320,7 +337,7 @@ static bool requests_ok(const awo_sim_request* reqs, int32_t n_req, uint64_t* to
         const awo_sim_request& q = reqs[i];
         if (!q.d_h || !q.d_count || !q.d_maxe || !grid_ok(q.grid)) return false;
         if (q.n_cells_max > 0 && !q.d_cells) return false;
-        if (!sim_params_ok(&q.params, q.grid.cell_size)) return false;
+        if (!sim_params_ok(&q.params, q.grid)) return false;
         if ((((uintptr_t)q.d_count) & 3u) != 0 || (((uintptr_t)q.d_maxe) & 3u) != 0) return false;
         tot += q.n_cells_max;
     }
@@ -337,7 +354,7 @@ extern "C" size_t awo_simulate_batched_workspace_bytes(const awo_sim_request* re
 {
     uint64_t tot = 0;
     if (!requests_ok(reqs, n_req, &tot)) return 0;
-    return BATCH_HEADER_BYTES + (size_t)tot * sizeof(CellStart);
+    return BATCH_HEADER_BYTES + (size_t)tot * sizeof(TexelStart);
 }
 
 extern "C" awo_status awo_simulate_batched(const awo_sim_request* reqs, int32_t n_req, const awo_tuning* tuning,
@@ -346,7 +363,7 @@ extern "C" awo_status awo_simulate_batched(const awo_sim_request* reqs, int32_t 
     uint64_t total = 0;
     if (!requests_ok(reqs, n_req, &total) || !tuning_ok(tuning) || !d_ws) return AWO_EINVAL;
     if ((((uintptr_t)d_ws) & 15u) != 0) return AWO_EINVAL;
-    if (ws_bytes < BATCH_HEADER_BYTES + (size_t)total * sizeof(CellStart)) return AWO_ENOMEM;
+    if (ws_bytes < BATCH_HEADER_BYTES + (size_t)total * sizeof(TexelStart)) return AWO_ENOMEM;
     const int threads = (tuning && tuning->threads_per_block) ? tuning->threads_per_block : 128;
     const uint32_t group = tuning ? (uint32_t)tuning->group_particles : 0u;
     const int refill = tuning ? tuning->refill : AWO_REFILL_LANE;
@@ -356,7 +373,7 @@ extern "C" awo_status awo_simulate_batched(const awo_sim_request* reqs, int32_t 
     memset(&a, 0, sizeof(a));
     a.n_req = (uint32_t)n_req;
     a.hdr = static_cast<BatchHeader*>(d_ws);
-    a.starts = reinterpret_cast<CellStart*>(static_cast<char*>(d_ws) + BATCH_HEADER_BYTES);
+    a.starts = reinterpret_cast<TexelStart*>(static_cast<char*>(d_ws) + BATCH_HEADER_BYTES);
     bool same_seed = true;
     uint32_t off = 0;
     for (int i = 0; i < n_req; ++i) {
@@ -387,6 +404,12 @@ extern "C" awo_status awo_simulate_batched(const awo_sim_request* reqs, int32_t 
         b.k1 = (uint32_t)(p->seed >> 32);
         b.starts_off = off;
         off += q.n_cells_max;
+        int64_t wr = 0, hr = 0;
+        release_texture_dims(q.grid, p->release_log2, &wr, &hr);  // checked by requests_ok
+        b.texel = p->release_log2 != 0 ? 1u : 0u;
+        b.tg.Wr = (uint32_t)wr;
+        b.tg.n_tex = (uint32_t)(wr * hr);
+        b.tg.scale = ldexpf(1.0f, -p->release_log2);
         if (p->seed != reqs[0].params.seed) same_seed = false;
         if (p->flags & AWO_SIM_CLEAR_OUTPUTS) {
             const size_t bytes = (size_t)cells_of(q.grid) * sizeof(uint32_t);

@@ -59,4 +59,27 @@ inline bool sim_params_ok(const awo_sim_params* p, float cs)
     return true;
 }
 
+// Size of the release texture at 2^r times the resolution of grid g
+// (awo_release_texture); false when r or the size is out of range.
+inline bool release_texture_dims(awo_grid g, int32_t r, int64_t* wr, int64_t* hr)
+{
+    if (!grid_ok(g) || r < -AWO_RELEASE_LOG2_MAX || r > AWO_RELEASE_LOG2_MAX) return false;
+    if (r >= 0) {
+        *wr = (int64_t)g.width << r;
+        *hr = (int64_t)g.height << r;
+    } else {
+        const int64_t q = (int64_t)1 << (-r);
+        *wr = ((int64_t)g.width + q - 1) / q;
+        *hr = ((int64_t)g.height + q - 1) / q;
+    }
+    return *wr * *hr < ((int64_t)1 << 31);
+}
+
+// Parameters and the release texture they name are valid for grid g.
+inline bool sim_params_ok(const awo_sim_params* p, awo_grid g)
+{
+    int64_t wr, hr;
+    return sim_params_ok(p, g.cell_size) && release_texture_dims(g, p->release_log2, &wr, &hr);
+}
+
 }  // namespace awo

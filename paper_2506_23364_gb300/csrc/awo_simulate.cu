@@ -33,6 +33,8 @@
 //  * Arithmetic is FP32 with explicit round-to-nearest intrinsics: no fused
 //    multiply-add, IEEE sqrt and reciprocal, so every particle follows the
 //    formulas of awo.h bit for bit.
+#include <math.h>
+
 #include "awo_particle.cuh"
 
 namespace awo {
@@ -61,8 +63,9 @@ struct SimArgs {
     uint32_t n_cells_max;
     uint32_t n_grid;       // W*H
     uint32_t N;
+    TexelGeom tg;          // release texture (texel mode only)
     SimWorkspace* ws;
-    CellStart* starts;     // one per release-list entry
+    void* starts;          // one start record per release-list entry (CellStart or TexelStart)
 };
 
 constexpr int SIM_THREADS = 128;
@@ -79,17 +82,26 @@ __device__ __forceinline__ uint32_t release_count(const SimArgs& a)
 // Prologue: per release-list entry, the start record and the release visit
 // of all N particles (count += N; their energy is 0, so the maximum is
 // unchanged).  Grid-stride over the entries, whose number may be on the device.
+// TEXELS: the entries are texels of the release texture.
+template <bool TEXELS>
 __global__ void __launch_bounds__(256) k_sim_starts(const __grid_constant__ SimArgs a)
 {
     const uint32_t n_cells = release_count(a);
     for (uint32_t ci = blockIdx.x * blockDim.x + threadIdx.x; ci < n_cells; ci += gridDim.x * blockDim.x) {
-        const uint32_t cell = __ldg(a.cells + ci);
-        const CellStart st = cell_start(a.h, a.W, a.H, a.n_grid, cell);
-        if (st.xy != ~0u) atomicAdd(a.count + cell, a.N);
-        a.starts[ci] = st;
+        const uint32_t entry = __ldg(a.cells + ci);
+        if (TEXELS) {
+            const TexelStart st = texel_start(a.h, a.W, a.H, a.tg, entry);
+            if (st.t != ~0u) atomicAdd(a.count + st.vcell, a.N);
+            static_cast<TexelStart*>(a.starts)[ci] = st;
+        } else {
+            const CellStart st = cell_start(a.h, a.W, a.H, a.n_grid, entry);
+            if (st.xy != ~0u) atomicAdd(a.count + entry, a.N);
+            static_cast<CellStart*>(a.starts)[ci] = st;
+        }
     }
 }
 
+template <bool TEXELS>
 __global__ void __launch_bounds__(SIM_THREADS) k_simulate(const __grid_constant__ SimArgs a)
 {
     const int lane = threadIdx.x & 31;
@@ -137,11 +149,21 @@ __global__ void __launch_bounds__(SIM_THREADS) k_simulate(const __grid_constant_
                 const bool mine = ((idle >> lane) & 1u) && rank < take;
                 uint32_t ci = cur_ci, jj = cur_j;
                 advance(ci, jj, rank < take ? rank : 0u, a.N);
-                uint4 st = make_uint4(~0u, 0u, 0u, 0u);
-                if (mine) st = __ldg(reinterpret_cast<const uint4*>(a.starts) + ci);
+                uint4 st = make_uint4(~0u, 0u, 0u, 0u), st1 = make_uint4(0u, 0u, 0u, 0u);
+                if (TEXELS) {
+                    if (mine) {
+                        st = __ldg(reinterpret_cast<const uint4*>(a.starts) + 2u * ci);
+                        st1 = __ldg(reinterpret_cast<const uint4*>(a.starts) + 2u * ci + 1u);
+                    }
+                } else {
+                    if (mine) st = __ldg(reinterpret_cast<const uint4*>(a.starts) + ci);
+                }
                 const bool ok = mine && st.x != ~0u;
                 my_bad += (mine && !ok) ? 1u : 0u;  // release index outside the grid: skipped, reported
-                AWO_LANE_START(ok, st, jj, a.W);
+                if (TEXELS)
+                    AWO_LANE_START_TEXEL(ok, st, st1, jj);
+                else
+                    AWO_LANE_START(ok, st, jj, a.W);
                 const bool cap0 = ok && a.max_steps == 0u;  // capped at the release visit
                 my_cap += cap0 ? 1u : 0u;
                 my_traj += cap0 ? 1u : 0u;
@@ -159,6 +181,7 @@ __global__ void __launch_bounds__(SIM_THREADS) k_simulate(const __grid_constant_
     AWO_FLUSH_COUNTERS(a.ws->stats);
 }
 
+template <bool TEXELS>
 static int sim_blocks_per_sm()
 {
     static int cached[64] = {0};
@@ -167,7 +190,8 @@ static int sim_blocks_per_sm()
     if (dev < 0 || dev >= 64) dev = 0;
     if (cached[dev] == 0) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_simulate, SIM_THREADS, 0) != cudaSuccess || b < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_simulate<TEXELS>, SIM_THREADS, 0) != cudaSuccess ||
+            b < 1)
             b = 1;
         cached[dev] = b;
     }
@@ -182,7 +206,7 @@ static size_t starts_offset() { return 256; }
 
 extern "C" size_t awo_simulate_workspace_bytes(uint32_t n_cells_max)
 {
-    return starts_offset() + (size_t)n_cells_max * sizeof(CellStart);
+    return starts_offset() + (size_t)n_cells_max * sizeof(TexelStart);
 }
 
 extern "C" awo_status awo_simulate(const float* d_h, awo_grid g, const uint32_t* d_cells, const uint32_t* d_n_cells,
@@ -191,7 +215,7 @@ extern "C" awo_status awo_simulate(const float* d_h, awo_grid g, const uint32_t*
 {
     if (!d_h || !d_count || !d_maxe || !d_ws || !grid_ok(g)) return AWO_EINVAL;
     if (n_cells_max > 0 && !d_cells) return AWO_EINVAL;
-    if (!sim_params_ok(p, g.cell_size)) return AWO_EINVAL;
+    if (!sim_params_ok(p, g)) return AWO_EINVAL;
     if ((((uintptr_t)d_ws) & 15u) != 0 || (((uintptr_t)d_count) & 3u) != 0 || (((uintptr_t)d_maxe) & 3u) != 0)
         return AWO_EINVAL;
     if (ws_bytes < awo_simulate_workspace_bytes(n_cells_max)) return AWO_ENOMEM;
@@ -234,13 +258,23 @@ extern "C" awo_status awo_simulate(const float* d_h, awo_grid g, const uint32_t*
     a.count = d_count;
     a.maxe = d_maxe;
     a.ws = ws;
-    a.starts = reinterpret_cast<CellStart*>(static_cast<char*>(d_ws) + starts_offset());
+    a.starts = static_cast<char*>(d_ws) + starts_offset();
+    int64_t wr = 0, hr = 0;
+    release_texture_dims(g, p->release_log2, &wr, &hr);  // checked by sim_params_ok
+    a.tg.Wr = (uint32_t)wr;
+    a.tg.n_tex = (uint32_t)(wr * hr);
+    a.tg.scale = ldexpf(1.0f, -p->release_log2);
+    const bool texels = p->release_log2 != 0;
 
     if (a.N > 0 && (n_cells_max > 0)) {
         const unsigned pro_blocks = stream_blocks((int64_t)n_cells_max, 256);
-        k_sim_starts<<<pro_blocks, 256, 0, s>>>(a);
-        unsigned blocks = (unsigned)(sm_count() * sim_blocks_per_sm());
-        k_simulate<<<blocks, SIM_THREADS, 0, s>>>(a);
+        if (texels) {
+            k_sim_starts<true><<<pro_blocks, 256, 0, s>>>(a);
+            k_simulate<true><<<(unsigned)(sm_count() * sim_blocks_per_sm<true>()), SIM_THREADS, 0, s>>>(a);
+        } else {
+            k_sim_starts<false><<<pro_blocks, 256, 0, s>>>(a);
+            k_simulate<false><<<(unsigned)(sm_count() * sim_blocks_per_sm<false>()), SIM_THREADS, 0, s>>>(a);
+        }
         awo_status st = launch_status();
         if (st != AWO_OK) return st;
     }

@@ -234,7 +234,7 @@ static awo_status soft_setup(SoftArgs& a, const float* d_h, awo_grid g, const ui
                              const uint32_t* d_n_cells, uint32_t n_cells_max, const float* d_weight,
                              const awo_sim_params* p, float tau, void* d_ws, size_t ws_bytes)
 {
-    if (!d_h || !d_ws || !grid_ok(g) || !sim_params_ok(p, g.cell_size)) return AWO_EINVAL;
+    if (!d_h || !d_ws || !grid_ok(g) || !sim_params_ok(p, g.cell_size) || p->release_log2 != 0) return AWO_EINVAL;
     if (n_cells_max > 0 && (!d_cells || !d_weight)) return AWO_EINVAL;
     if (!(tau > 0.0f) || !(tau < 3.0e38f)) return AWO_EINVAL;
     if ((((uintptr_t)d_ws) & 15u) != 0) return AWO_EINVAL;

@@ -220,6 +220,68 @@ __global__ void __launch_bounds__(RT_THREADS) k_mask_scatter(const uint8_t* __re
     }
 }
 
+// Release points on a texture at 2^r times the DEM resolution
+// (awo_release_texture): per tile of RT_TILE texels, the mask and its count.
+// A texel's steepness is the bilinear interpolation of tan^2 at its centre,
+// with the footprint rule and FP32 weights of the particles' height sampling.
+__device__ __forceinline__ float texel_centre(uint32_t a, float scale, float n_m1)
+{
+    const float c = __fsub_rn(__fmul_rn(__fadd_rn(__uint2float_rn(a), 0.5f), scale), 0.5f);
+    return fminf(fmaxf(c, 0.0f), n_m1);
+}
+
+__global__ void __launch_bounds__(RT_THREADS) k_release_texture_mask(const float* __restrict__ tan2, int W, int H,
+                                                                     uint32_t Wr, int64_t n, float scale,
+                                                                     float t_lo, float t_hi,
+                                                                     uint8_t* __restrict__ mask,
+                                                                     uint32_t* __restrict__ tile_count)
+{
+    const int64_t base = (int64_t)blockIdx.x * RT_TILE + (int64_t)threadIdx.x * RT_CELLS;
+    const float wm1 = __int2float_rn(W - 1), hm1 = __int2float_rn(H - 1);
+    uint32_t b = 0u, a = 0u;
+    if (base < n) {
+        b = (uint32_t)(base / Wr);
+        a = (uint32_t)(base - (int64_t)b * Wr);
+    }
+    float v = texel_centre(b, scale, hm1);
+    int cnt = 0;
+    uint32_t packed[RT_CELLS / 4] = {0u, 0u, 0u, 0u};
+#pragma unroll 4
+    for (int k = 0; k < RT_CELLS; ++k) {
+        if (base + k < n) {
+            const float u = texel_centre(a, scale, wm1);
+            const int i0 = __float2int_rd(u), j0 = __float2int_rd(v);
+            const float fx = __fsub_rn(u, __int2float_rn(i0)), fy = __fsub_rn(v, __int2float_rn(j0));
+            const int di = i0 + 1 < W ? 1 : 0;
+            const int dj = j0 + 1 < H ? W : 0;
+            const int o = j0 * W + i0;
+            const float t00 = __ldg(tan2 + o), t10 = __ldg(tan2 + o + di);
+            const float t01 = __ldg(tan2 + o + dj), t11 = __ldg(tan2 + o + dj + di);
+            const float ox = __fsub_rn(1.0f, fx), oy = __fsub_rn(1.0f, fy);
+            const float top = __fadd_rn(__fmul_rn(t00, ox), __fmul_rn(t10, fx));
+            const float bot = __fadd_rn(__fmul_rn(t01, ox), __fmul_rn(t11, fx));
+            const float T = __fadd_rn(__fmul_rn(top, oy), __fmul_rn(bot, fy));
+            const uint32_t sel = (t_lo <= T && T <= t_hi) ? 1u : 0u;
+            cnt += (int)sel;
+            packed[k >> 2] |= sel << (8 * (k & 3));
+            if (++a == Wr) {
+                a = 0u;
+                ++b;
+                v = texel_centre(b, scale, hm1);
+            }
+        }
+    }
+    if (base + RT_CELLS <= n && (((uintptr_t)(mask + base)) & 15u) == 0) {
+        *reinterpret_cast<uint4*>(mask + base) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    } else {
+        for (int k = 0; k < RT_CELLS; ++k)
+            if (base + k < n) mask[base + k] = (uint8_t)((packed[k >> 2] >> (8 * (k & 3))) & 0xffu);
+    }
+    int total;
+    block_exclusive_scan(cnt, &total);
+    if (threadIdx.x == 0) tile_count[blockIdx.x] = (uint32_t)total;
+}
+
 static float tan2_of_degrees(double deg)
 {
     double t = tan(deg * (3.14159265358979323846 / 180.0));
@@ -363,5 +425,50 @@ extern "C" awo_status awo_release_from_mask(const uint8_t* d_mask, awo_grid g, u
     k_mask_count<<<tiles, RT_THREADS, 0, s>>>(d_mask, n, tile_count);
     k_release_scan<<<1, 1024, 0, s>>>(tile_count, tiles, tile_offset, d_n);
     k_mask_scatter<<<tiles, RT_THREADS, 0, s>>>(d_mask, n, tile_offset, d_cells);
+    return launch_status();
+}
+
+// ---------------------------------------------------------------------------
+// b''. Release points on a texture of chosen resolution: mask and tile counts
+// in one pass, then the scan and the ordered scatter of the mask's texels.
+// ---------------------------------------------------------------------------
+extern "C" awo_status awo_release_texture_dims(awo_grid g, int32_t release_log2, int32_t* width, int32_t* height)
+{
+    int64_t wr, hr;
+    if (!width || !height || !release_texture_dims(g, release_log2, &wr, &hr)) return AWO_EINVAL;
+    *width = (int32_t)wr;
+    *height = (int32_t)hr;
+    return AWO_OK;
+}
+
+extern "C" size_t awo_release_texture_workspace_bytes(awo_grid g, int32_t release_log2)
+{
+    int64_t wr, hr;
+    if (!release_texture_dims(g, release_log2, &wr, &hr)) return 0;
+    const int64_t tiles = (wr * hr + RT_TILE - 1) / RT_TILE;
+    return (size_t)(2 * tiles * sizeof(uint32_t) + 256);
+}
+
+extern "C" awo_status awo_release_texture(const float* d_tan2, awo_grid g, int32_t release_log2, double slope_lo_deg,
+                                          double slope_hi_deg, uint8_t* d_mask, uint32_t* d_texels, uint32_t* d_n,
+                                          void* d_ws, size_t ws_bytes, void* stream)
+{
+    int64_t wr, hr;
+    if (!d_tan2 || !d_mask || !d_texels || !d_n || !d_ws || !release_texture_dims(g, release_log2, &wr, &hr))
+        return AWO_EINVAL;
+    if (!(slope_lo_deg >= 0.0) || !(slope_hi_deg < 90.0) || slope_lo_deg > slope_hi_deg) return AWO_EINVAL;
+    if ((((uintptr_t)d_ws) & 15u) != 0) return AWO_EINVAL;
+    if (ws_bytes < awo_release_texture_workspace_bytes(g, release_log2)) return AWO_ENOMEM;
+    const int64_t n = wr * hr;
+    const int tiles = (int)((n + RT_TILE - 1) / RT_TILE);
+    uint32_t* tile_count = static_cast<uint32_t*>(d_ws);
+    uint32_t* tile_offset = tile_count + tiles;
+    const float t_lo = tan2_of_degrees(slope_lo_deg), t_hi = tan2_of_degrees(slope_hi_deg);
+    const float scale = ldexpf(1.0f, -release_log2);
+    cudaStream_t s = as_stream(stream);
+    k_release_texture_mask<<<tiles, RT_THREADS, 0, s>>>(d_tan2, g.width, g.height, (uint32_t)wr, n, scale, t_lo,
+                                                        t_hi, d_mask, tile_count);
+    k_release_scan<<<1, 1024, 0, s>>>(tile_count, tiles, tile_offset, d_n);
+    k_mask_scatter<<<tiles, RT_THREADS, 0, s>>>(d_mask, n, tile_offset, d_texels);
     return launch_status();
 }

@@ -13,7 +13,8 @@ import numpy as np
 import torch
 
 from . import (AWO_OK, Grid, SimParams, awo_decode_u16, awo_finalize, awo_normals, awo_overlay_lod,
-               awo_release, awo_release_from_mask, awo_release_workspace_bytes, awo_simulate,
+               awo_release, awo_release_from_mask, awo_release_texture, awo_release_texture_dims,
+               awo_release_texture_workspace_bytes, awo_release_workspace_bytes, awo_simulate,
                awo_simulate_workspace_bytes, grid, lod_shapes, stats_dict)
 
 SIM_CLEAR_OUTPUTS = 1
@@ -24,26 +25,42 @@ def _ws(nbytes: int, device) -> torch.Tensor:
 
 
 class Overlay:
-    """Device buffers and call sequence for one W x H workflow."""
+    """Device buffers and call sequence for one W x H workflow.
+
+    ``release_log2`` = r evaluates release points on a texture at 2^r times
+    the DEM's resolution (r in -3..3; 0: one per cell): the mask and the
+    release list are then at that texture's resolution, and the particles
+    start at texel centres."""
 
     def __init__(self, width: int, height: int, cell_size: float, *, quantised: bool, levels: int = 1,
-                 device="cuda", want_normals: bool = True, want_slope: bool = False, want_mask: bool = True):
+                 device="cuda", want_normals: bool = True, want_slope: bool = False, want_mask: bool = True,
+                 release_log2: int = 0):
         self.g: Grid = grid(width, height, cell_size)
         self.levels = int(levels)
         self.quantised = quantised
+        self.release_log2 = int(release_log2)
         d = torch.device(device)
         self.device = d
-        n = self.g.cells
+        if self.release_log2:
+            wr, hr = awo_release_texture_dims(self.g, self.release_log2)
+            self.g_rel: Grid = grid(wr, hr, cell_size * 2.0 ** (-self.release_log2))
+        else:
+            self.g_rel = self.g
+        n_rel = self.g_rel.cells
+        self.n_tex = n_rel
         self.q = torch.empty((height, width), dtype=torch.int16, device=d) if quantised else None
         self.h = torch.empty((height, width), dtype=torch.float32, device=d)
         self.normal = torch.empty((3, height, width), dtype=torch.float32, device=d) if want_normals else None
         self.tan2 = torch.empty((height, width), dtype=torch.float32, device=d)
         self.slope = torch.empty((height, width), dtype=torch.float32, device=d) if want_slope else None
-        self.mask = torch.empty((height, width), dtype=torch.uint8, device=d) if want_mask else None
-        self.cells = torch.empty(n, dtype=torch.int32, device=d)
+        want_mask = want_mask or bool(self.release_log2)  # the texture path needs its mask
+        self.mask = torch.empty((self.g_rel.height, self.g_rel.width), dtype=torch.uint8, device=d) \
+            if want_mask else None
+        self.cells = torch.empty(n_rel, dtype=torch.int32, device=d)
         self.n_rel = torch.zeros(1, dtype=torch.int32, device=d)
-        self.ws_rel = _ws(awo_release_workspace_bytes(self.g), d)
-        self.ws_sim = _ws(awo_simulate_workspace_bytes(n), d)
+        self.ws_rel = _ws(awo_release_texture_workspace_bytes(self.g, self.release_log2) if self.release_log2
+                          else awo_release_workspace_bytes(self.g), d)
+        self.ws_sim = _ws(awo_simulate_workspace_bytes(n_rel), d)
         self.count = torch.zeros((height, width), dtype=torch.int32, device=d)
         self.maxe = torch.zeros((height, width), dtype=torch.float32, device=d)
         self.vel = torch.empty((height, width), dtype=torch.float32, device=d)
@@ -67,23 +84,29 @@ class Overlay:
         if self.quantised:
             awo_decode_u16(self.q, self.g, decode_scale, self.h, stream)
         awo_normals(self.h, self.g, self.normal, self.tan2, self.slope, stream)
-        awo_release(self.tan2, self.g, slope_lo_deg, slope_hi_deg, self.mask, self.cells, self.n_rel, self.ws_rel,
-                    stream)
+        if self.release_log2:
+            awo_release_texture(self.tan2, self.g, self.release_log2, slope_lo_deg, slope_hi_deg, self.mask,
+                                self.cells, self.n_rel, self.ws_rel, stream)
+        else:
+            awo_release(self.tan2, self.g, slope_lo_deg, slope_hi_deg, self.mask, self.cells, self.n_rel,
+                        self.ws_rel, stream)
 
     def terrain_from_mask(self, mask: torch.Tensor, decode_scale: float = 0.1, stream=None):
-        """a0-b': decode, normals and the release list from a caller's uint8 mask."""
+        """a0-b': decode, normals and the release list from a caller's uint8
+        mask (at the release texture's resolution)."""
         if self.quantised:
             awo_decode_u16(self.q, self.g, decode_scale, self.h, stream)
         awo_normals(self.h, self.g, self.normal, self.tan2, self.slope, stream)
-        awo_release_from_mask(mask, self.g, self.cells, self.n_rel, self.ws_rel, stream)
+        awo_release_from_mask(mask, self.g_rel, self.cells, self.n_rel, self.ws_rel, stream)
 
     def simulate(self, params: SimParams, clear: bool = True, stream=None, cells=None, n_cells=None):
         """c: particles from the release list (or from the given cells)."""
         p = SimParams.from_buffer_copy(params)
+        p.release_log2 = self.release_log2
         if clear:
             p.flags |= SIM_CLEAR_OUTPUTS
         if cells is None:
-            awo_simulate(self.h, self.g, self.cells, self.n_rel, self.g.cells, p, self.count, self.maxe, self.stats,
+            awo_simulate(self.h, self.g, self.cells, self.n_rel, self.n_tex, p, self.count, self.maxe, self.stats,
                          self.ws_sim, stream)
         else:
             awo_simulate(self.h, self.g, cells, None, int(n_cells), p, self.count, self.maxe, self.stats,

@@ -110,3 +110,37 @@ def test_batched_structs_and_host_validation(L):
     assert L.awo_simulate_batched(arr2, 2, None, None, fake, 1 << 20, None) == awo.AWO_EINVAL
     best = awo.Tuning()
     assert L.awo_tune_batched(arr, 0, fake, ws_need, None, ctypes.byref(best), None) == awo.AWO_EINVAL
+
+
+def test_release_texture_host_side(L):
+    """Texture sizes, workspace sizes and argument checks of the release
+    texture (no device work: validation fails before any launch)."""
+    G = awo.grid(5, 3, 10.0)
+    for r, want in ((0, (5, 3)), (1, (10, 6)), (3, (40, 24)), (-1, (3, 2)), (-3, (1, 1))):
+        assert awo.awo_release_texture_dims(G, r) == want
+    for r in (4, -4):
+        with pytest.raises(awo.AwoError):
+            awo.awo_release_texture_dims(G, r)
+    with pytest.raises(awo.AwoError):
+        awo.awo_release_texture_dims(awo.grid(65536, 8192, 1.0), 1)  # 2^31 texels
+    g8 = awo.grid(8192, 8192, 10.0)
+    assert awo.awo_release_texture_workspace_bytes(g8, 0) == awo.awo_release_workspace_bytes(g8)
+    assert awo.awo_release_texture_workspace_bytes(g8, 1) >= 2 * 4 * (4 * 8192 * 8192 // 4096)
+    assert awo.awo_release_texture_workspace_bytes(g8, 5) == 0
+    fake = ctypes.c_void_p(256)
+    G16 = awo.grid(16, 16, 10.0)
+    ws = awo.awo_release_texture_workspace_bytes(G16, 2)
+    assert L.awo_release_texture(fake, G16, 2, 30.0, 45.0, None, fake, fake, fake, ws, None) == awo.AWO_EINVAL
+    assert L.awo_release_texture(fake, G16, 4, 30.0, 45.0, fake, fake, fake, fake, ws, None) == awo.AWO_EINVAL
+    assert L.awo_release_texture(fake, G16, 2, 45.0, 30.0, fake, fake, fake, fake, ws, None) == awo.AWO_EINVAL
+    assert L.awo_release_texture(fake, G16, 2, 30.0, 45.0, fake, fake, fake, fake, ws - 1, None) == awo.AWO_ENOMEM
+    # particle parameters naming a texture out of range
+    for r in (4, -4):
+        p = awo.SimParams.make(release_log2=r)
+        assert L.awo_simulate(fake, G16, fake, None, 4, ctypes.byref(p), fake, fake, None, fake, 1 << 20,
+                              None) == awo.AWO_EINVAL
+    # soft mode takes DEM cells only
+    p = awo.SimParams.make(release_log2=1)
+    assert L.awo_soft_forward(fake, G16, fake, None, 4, fake, ctypes.byref(p), ctypes.c_float(1.0), fake, None,
+                              fake, 1 << 20, None) == awo.AWO_EINVAL
+    assert ctypes.sizeof(awo.SimParams) == 48 and awo.SimParams.release_log2.offset == 44
