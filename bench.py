@@ -70,6 +70,7 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-threads", type=int, default=0, help="host threads of the oracle (0 = all cores)")
     ap.add_argument("--release-log2", type=int, default=0,
                     help="evaluate release points on a texture at 2^r x the DEM resolution (large/mid/tiny)")
     return ap.parse_args()
@@ -381,7 +382,7 @@ def run_awo(args, R: Ranks):
             "roofline_hbm": roofline_hbm,
             "clocks": clk, "kernel_sha": sha}
     if R.rank == 0 and R.world == 1 and not args.no_cpu_baseline and not args.release_log2:
-        line["cpu_baseline"] = _cpu_baseline(w, args.cpu_seconds)
+        line["cpu_baseline"] = _cpu_baseline(w, args.cpu_seconds, args.cpu_threads or None)
     if R.rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -658,7 +659,8 @@ def run_parabola(args, R: Ranks):
 def run_stages(args, R: Ranks):
     """Each streaming (HBM-bound) stage alone on the 8192^2 workload's rasters,
     CUDA-event timed (median of --steps after --warmup), against the measured
-    HBM copy bandwidth, with the algorithmic bytes of the design doc."""
+    HBM copy bandwidth.  Algorithmic bytes are each stage's inputs read once
+    and outputs written once (a release pass: tan^2 in, mask and list out)."""
     import torch
 
     import paper_2506_23364_gb300 as awo
@@ -681,12 +683,26 @@ def run_stages(args, R: Ranks):
     sp = awo.SnowParams(1500.0, 300.0, 36.0, 4.0)
     nz = ov.normal[2]
     lv_bytes = sum(c.numel() * 8 for c in ov.count_lv)
+    # release on the texture at 2x the DEM resolution (4 texels per cell)
+    wr, hr = awo.awo_release_texture_dims(g, 1)
+    mask_t = torch.empty(wr * hr, dtype=torch.uint8, device=R.device)
+    tex = torch.empty(wr * hr, dtype=torch.int32, device=R.device)
+    n_tex = torch.zeros(1, dtype=torch.int32, device=R.device)
+    ws_t = torch.empty(awo.awo_release_texture_workspace_bytes(g, 1), dtype=torch.uint8, device=R.device)
+
+    def rel_tex():
+        awo.awo_release_texture(ov.tan2, g, 1, w.slope_lo_deg, w.slope_hi_deg, mask_t, tex, n_tex, ws_t)
+
+    rel_tex()
+    torch.cuda.synchronize()
+    n_rel_t = int(n_tex.item())
     stages = [
         ("decode", lambda: awo.awo_decode_u16(ov.q, g, 0.1, ov.h), 6 * n),
         ("normals (+tan2)", lambda: awo.awo_normals(ov.h, g, ov.normal, ov.tan2, None), 20 * n),
         ("normals (+tan2, slope_deg)", lambda: awo.awo_normals(ov.h, g, ov.normal, ov.tan2, ov.slope), 24 * n),
         ("release (3 passes)", lambda: awo.awo_release(ov.tan2, g, w.slope_lo_deg, w.slope_hi_deg, ov.mask, ov.cells,
-                                                       ov.n_rel, ov.ws_rel), 9 * n + 4 * n_rel),
+                                                       ov.n_rel, ov.ws_rel), 5 * n + 4 * n_rel),
+        ("release texture 2x (3 passes)", rel_tex, 4 * n + wr * hr + 4 * n_rel_t),
         ("finalize", lambda: awo.awo_finalize(ov.maxe, g, 9.81, ov.vel), 8 * n),
         ("mipmap (5 levels)", lambda: awo.awo_overlay_lod(ov.count, ov.vel, g, w.lod_levels, ov.count_lv, ov.vel_lv),
          8 * n + lv_bytes),
@@ -711,7 +727,8 @@ def run_stages(args, R: Ranks):
         gbs = nbytes / (ms / 1e3) / 1e9
         rows.append({"stage": name, "ms": ms, "alg_bytes": nbytes, "GB/s": gbs, "frac_hbm": gbs / hbm})
     line = {"metric": "streaming stages at 8192^2: GB/s of algorithmic bytes vs measured HBM copy bandwidth",
-            "unit": "GB/s", "hbm_peak_gbs": hbm, "config": {"workload": w.name, "cells": n, "release_cells": n_rel},
+            "unit": "GB/s", "hbm_peak_gbs": hbm, "config": {"workload": w.name, "cells": n, "release_cells": n_rel,
+                                                            "release_texels_2x": n_rel_t},
             "stages": rows}
     if R.rank == 0:
         print(json.dumps(line), flush=True)
@@ -725,15 +742,25 @@ def run_reference(args, R: Ranks):
     import numpy as np
 
     import oracle
+    from paper_2506_23364_gb300 import inputs
 
-    w = _workload(args.workload, args.crop)
-    h = oracle.decode_u16(w.dem_u16) if w.dem_u16 is not None else w.dem_f32
-    _, t2, _ = oracle.normals(h, w.cell_size, want_slope=False)
-    _, cells = oracle.release(t2, w.slope_lo_deg, w.slope_hi_deg)
+    if args.workload not in ("large", "mid", "tiny", "parabola"):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the large, mid, tiny and "
+                                                               "parabola workloads"}), flush=True)
+        return
+    if args.workload == "parabola":
+        w = inputs.parabola()
+        h = w.dem_f32
+        cells = np.flatnonzero(inputs.parabola_release_mask().ravel()).astype(np.uint32)
+    else:
+        w = _workload(args.workload, args.crop)
+        h = oracle.decode_u16(w.dem_u16) if w.dem_u16 is not None else w.dem_f32
+        _, t2, _ = oracle.normals(h, w.cell_size, want_slope=False)
+        _, cells = oracle.release(t2, w.slope_lo_deg, w.slope_hi_deg)
     p = oracle.SimParams(mu=w.mu, drag_k=w.drag_k, persistence=w.persistence, randomness=w.randomness,
                          step_scale=w.step_scale, gravity=w.gravity, traj_per_cell=w.traj_per_cell,
                          max_steps=w.max_steps, seed=w.seed)
-    threads = os.cpu_count() or 1
+    threads = args.cpu_threads or os.cpu_count() or 1
     total = args.steps + max(args.warmup, 0)
     per_step_s = max(1.0, min(10.0, 150.0 / max(total, 1)))
     rng = np.random.default_rng(777)

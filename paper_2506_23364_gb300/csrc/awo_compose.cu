@@ -17,33 +17,75 @@ __device__ __forceinline__ uint8_t to_u8(float x)
     return (uint8_t)__float2uint_rn(x);
 }
 
-__global__ void k_compose(const float* __restrict__ value, const uint32_t* __restrict__ count, int64_t n,
-                          const awo_colormap cm, const uint8_t* __restrict__ base, uint8_t* __restrict__ out)
+// The colour ramp in shared memory (stop values and colours as floats), so
+// that per-texel lookups with a data-dependent stop index stay on chip.
+struct RampSmem {
+    float value[16];
+    float rgb[16][3];
+};
+
+// One texel: colour of value x, opacity from its count, over base texel b
+// (packed RGBA, little-endian bytes) when there is a base.  The segment is
+// the number of interior stops at or below x (stops strictly increase), a
+// loop of uniform trip count over the broadcast stop values.
+__device__ __forceinline__ uint32_t compose_one(const RampSmem& r, int n_stops, float alpha, uint32_t count_min,
+                                                float x, uint32_t count, bool has_base, uint32_t b)
 {
-    const int last = cm.n_stops - 1;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        float x = value[i];
-        if (!(x > cm.value[0])) x = cm.value[0];
-        if (x > cm.value[last]) x = cm.value[last];
-        int k = 0;
-        while (k + 1 < last && x >= cm.value[k + 1]) ++k;
-        const float t = __fdiv_rn(__fsub_rn(x, cm.value[k]), __fsub_rn(cm.value[k + 1], cm.value[k]));
-        const float a = count[i] >= cm.count_min ? cm.alpha : 0.0f;
-        uchar4 o;
-        uint8_t ch[3];
+    const int last = n_stops - 1;
+    if (!(x > r.value[0])) x = r.value[0];
+    if (x > r.value[last]) x = r.value[last];
+    int k = 0;
+    for (int j = 1; j < last; ++j) k += x >= r.value[j] ? 1 : 0;
+    const float t = __fdiv_rn(__fsub_rn(x, r.value[k]), __fsub_rn(r.value[k + 1], r.value[k]));
+    const float a = count >= count_min ? alpha : 0.0f;
+    uint32_t o = 0u;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float c0 = (float)cm.rgb[k][c], c1 = (float)cm.rgb[k + 1][c];
-            const float col = __fadd_rn(c0, __fmul_rn(t, __fsub_rn(c1, c0)));
-            ch[c] = base ? to_u8(__fadd_rn(__fmul_rn(a, col), __fmul_rn(__fsub_rn(1.0f, a), (float)base[4 * i + c])))
-                         : to_u8(col);
-        }
-        o.x = ch[0];
-        o.y = ch[1];
-        o.z = ch[2];
-        o.w = base ? base[4 * i + 3] : to_u8(__fmul_rn(255.0f, a));
-        reinterpret_cast<uchar4*>(out)[i] = o;
+    for (int c = 0; c < 3; ++c) {
+        const float c0 = r.rgb[k][c], c1 = r.rgb[k + 1][c];
+        const float col = __fadd_rn(c0, __fmul_rn(t, __fsub_rn(c1, c0)));
+        const float bc = (float)((b >> (8 * c)) & 0xffu);
+        const uint8_t ch = has_base ? to_u8(__fadd_rn(__fmul_rn(a, col), __fmul_rn(__fsub_rn(1.0f, a), bc)))
+                                    : to_u8(col);
+        o |= (uint32_t)ch << (8 * c);
     }
+    const uint32_t oa = has_base ? (b >> 24) : (uint32_t)to_u8(__fmul_rn(255.0f, a));
+    return o | (oa << 24);
+}
+
+// Four texels per thread (float4 / uint4 loads, uint4 store) when every
+// buffer is 16-byte aligned, then a scalar tail.
+__global__ void k_compose(const float* __restrict__ value, const uint32_t* __restrict__ count, int64_t n,
+                          const __grid_constant__ awo_colormap cm, const uint8_t* __restrict__ base,
+                          uint8_t* __restrict__ out, bool vec4)
+{
+    __shared__ RampSmem ramp;
+    for (int i = threadIdx.x; i < 16; i += blockDim.x) {
+        ramp.value[i] = cm.value[i];
+        ramp.rgb[i][0] = (float)cm.rgb[i][0];
+        ramp.rgb[i][1] = (float)cm.rgb[i][1];
+        ramp.rgb[i][2] = (float)cm.rgb[i][2];
+    }
+    __syncthreads();
+    const int ns = cm.n_stops;
+    const float alpha = cm.alpha;
+    const uint32_t cmin = cm.count_min;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool has_base = base != nullptr;
+    const uint32_t* base32 = reinterpret_cast<const uint32_t*>(base);
+    uint32_t* out32 = reinterpret_cast<uint32_t*>(out);
+    const int64_t n4 = vec4 ? n / 4 : 0;
+    for (int64_t q = tid; q < n4; q += stride) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(value) + q);
+        const uint4 c = __ldg(reinterpret_cast<const uint4*>(count) + q);
+        const uint4 b = has_base ? __ldg(reinterpret_cast<const uint4*>(base32) + q) : make_uint4(0u, 0u, 0u, 0u);
+        reinterpret_cast<uint4*>(out32)[q] = make_uint4(compose_one(ramp, ns, alpha, cmin, v.x, c.x, has_base, b.x),
+                                                        compose_one(ramp, ns, alpha, cmin, v.y, c.y, has_base, b.y),
+                                                        compose_one(ramp, ns, alpha, cmin, v.z, c.z, has_base, b.z),
+                                                        compose_one(ramp, ns, alpha, cmin, v.w, c.w, has_base, b.w));
+    }
+    for (int64_t i = 4 * n4 + tid; i < n; i += stride)
+        out32[i] = compose_one(ramp, ns, alpha, cmin, value[i], count[i], has_base, has_base ? base32[i] : 0u);
 }
 
 __device__ __forceinline__ float smooth_step(float e0, float e1, float x)
@@ -54,13 +96,32 @@ __device__ __forceinline__ float smooth_step(float e0, float e1, float x)
     return __fmul_rn(__fmul_rn(t, t), __fsub_rn(3.0f, __fmul_rn(2.0f, t)));
 }
 
+__device__ __forceinline__ uint32_t snow_rgba(float a) { return 0x00ffffffu | ((uint32_t)to_u8(__fmul_rn(255.0f, a)) << 24); }
+
+// Four texels per thread when every buffer is 16-byte aligned, then a scalar tail.
 __global__ void k_snow(const float* __restrict__ h, const float* __restrict__ nz, int64_t n, float a0, float a1,
-                       float c0, float c1, float* __restrict__ alpha, uint8_t* __restrict__ rgba)
+                       float c0, float c1, float* __restrict__ alpha, uint8_t* __restrict__ rgba, bool vec4)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t* rgba32 = reinterpret_cast<uint32_t*>(rgba);
+    const int64_t n4 = vec4 ? n / 4 : 0;
+    for (int64_t q = tid; q < n4; q += stride) {
+        const float4 hv = __ldg(reinterpret_cast<const float4*>(h) + q);
+        const float4 zv = __ldg(reinterpret_cast<const float4*>(nz) + q);
+        const float4 a = make_float4(__fmul_rn(smooth_step(a0, a1, hv.x), smooth_step(c0, c1, zv.x)),
+                                     __fmul_rn(smooth_step(a0, a1, hv.y), smooth_step(c0, c1, zv.y)),
+                                     __fmul_rn(smooth_step(a0, a1, hv.z), smooth_step(c0, c1, zv.z)),
+                                     __fmul_rn(smooth_step(a0, a1, hv.w), smooth_step(c0, c1, zv.w)));
+        if (alpha) reinterpret_cast<float4*>(alpha)[q] = a;
+        if (rgba)
+            reinterpret_cast<uint4*>(rgba32)[q] = make_uint4(snow_rgba(a.x), snow_rgba(a.y), snow_rgba(a.z),
+                                                             snow_rgba(a.w));
+    }
+    for (int64_t i = 4 * n4 + tid; i < n; i += stride) {
         const float a = __fmul_rn(smooth_step(a0, a1, h[i]), smooth_step(c0, c1, nz[i]));
         if (alpha) alpha[i] = a;
-        if (rgba) reinterpret_cast<uchar4*>(rgba)[i] = make_uchar4(255, 255, 255, to_u8(__fmul_rn(255.0f, a)));
+        if (rgba) rgba32[i] = snow_rgba(a);
     }
 }
 
@@ -79,8 +140,10 @@ extern "C" awo_status awo_compose(const float* d_value, const uint32_t* d_count,
         if (!(cm->value[k] < cm->value[k + 1])) return AWO_EINVAL;
     if ((((uintptr_t)d_out_rgba) & 3u) != 0 || (((uintptr_t)d_base_rgba) & 3u) != 0) return AWO_EINVAL;
     const int64_t n = cells_of(g);
-    k_compose<<<stream_blocks(n, 256), 256, 0, as_stream(stream)>>>(d_value, d_count, n, *cm, d_base_rgba,
-                                                                     d_out_rgba);
+    const bool vec4 = ((((uintptr_t)d_value) | ((uintptr_t)d_count) | ((uintptr_t)d_base_rgba) |
+                        ((uintptr_t)d_out_rgba)) & 15u) == 0;
+    k_compose<<<stream_blocks(vec4 ? n / 4 + 1 : n, 256), 256, 0, as_stream(stream)>>>(d_value, d_count, n, *cm,
+                                                                                        d_base_rgba, d_out_rgba, vec4);
     return launch_status();
 }
 
@@ -101,6 +164,8 @@ extern "C" awo_status awo_snow_cover(const float* d_h, const float* d_nz, awo_gr
     if (s_hi < 0.0) s_hi = 0.0;
     const float c0 = (float)cos(s_lo * r), c1 = (float)cos(s_hi * r);
     const int64_t n = cells_of(g);
-    k_snow<<<stream_blocks(n, 256), 256, 0, as_stream(stream)>>>(d_h, d_nz, n, a0, a1, c0, c1, d_alpha, d_rgba);
+    const bool vec4 = ((((uintptr_t)d_h) | ((uintptr_t)d_nz) | ((uintptr_t)d_alpha) | ((uintptr_t)d_rgba)) & 15u) == 0;
+    k_snow<<<stream_blocks(vec4 ? n / 4 + 1 : n, 256), 256, 0, as_stream(stream)>>>(d_h, d_nz, n, a0, a1, c0, c1,
+                                                                                     d_alpha, d_rgba, vec4);
     return launch_status();
 }

@@ -32,46 +32,108 @@ int sm_count()
 // ---------------------------------------------------------------------------
 // a0. decode: h = (float)q * scale
 // ---------------------------------------------------------------------------
-__global__ void k_decode_u16(const uint16_t* __restrict__ q, int64_t n, float scale, float* __restrict__ h)
+// Four heights per thread (8-byte load, float4 store) when both buffers allow
+// it, then a scalar tail.
+__global__ void k_decode_u16(const uint16_t* __restrict__ q, int64_t n, float scale, float* __restrict__ h, bool vec4)
 {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        h[i] = __fmul_rn(__uint2float_rn((unsigned)q[i]), scale);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n4 = vec4 ? n / 4 : 0;
+    for (int64_t k = tid; k < n4; k += stride) {
+        const uint2 w = __ldg(reinterpret_cast<const uint2*>(q) + k);
+        reinterpret_cast<float4*>(h)[k] = make_float4(__fmul_rn(__uint2float_rn(w.x & 0xffffu), scale),
+                                                      __fmul_rn(__uint2float_rn(w.x >> 16), scale),
+                                                      __fmul_rn(__uint2float_rn(w.y & 0xffffu), scale),
+                                                      __fmul_rn(__uint2float_rn(w.y >> 16), scale));
+    }
+    for (int64_t i = 4 * n4 + tid; i < n; i += stride) h[i] = __fmul_rn(__uint2float_rn((unsigned)q[i]), scale);
 }
 
 // ---------------------------------------------------------------------------
-// a1. normals + tan^2 + optional slope in degrees.  One thread per cell of a
-// row segment; neighbours come through L1/L2 (each height is read by <= 5
-// threads of nearby warps).
+// a1. normals + tan^2 + optional slope in degrees.  One thread per run of 4
+// cells of a row (no 64-bit division: a 32-bit item index splits into row and
+// run).  When rows are 16-byte aligned (W % 4 == 0 and aligned buffers) the
+// run's heights, the rows above and below and the outputs move as float4;
+// the two horizontal neighbours outside the run are scalar loads (L1 hits).
+// Otherwise each cell is handled alone with the same arithmetic.
 // ---------------------------------------------------------------------------
-__global__ void k_normals(const float* __restrict__ h, int W, int H, float cs, float* __restrict__ nrm,
-                          float* __restrict__ tan2, float* __restrict__ slope_deg)
+__device__ __forceinline__ void normal_of(float gx, float gy, float& nx, float& ny, float& nz, float& t2)
+{
+    t2 = __fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy));
+    const float inv = __frcp_rn(__fsqrt_rn(__fadd_rn(t2, 1.0f)));
+    nx = __fmul_rn(-gx, inv);
+    ny = __fmul_rn(-gy, inv);
+    nz = inv;
+}
+
+__device__ __forceinline__ float slope_deg_of(float t2) { return atanf(sqrtf(t2)) * 57.295779513082320876f; }
+
+__global__ void __launch_bounds__(256) k_normals(const float* __restrict__ h, int W, int H, float cs,
+                                                 float* __restrict__ nrm, float* __restrict__ tan2,
+                                                 float* __restrict__ slope_deg, bool vec4)
 {
     const int64_t plane = (int64_t)W * H;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += stride) {
-        int y = (int)(i / W);
-        int x = (int)(i - (int64_t)y * W);
-        int xl = x > 0 ? x - 1 : 0, xr = x < W - 1 ? x + 1 : W - 1;
-        int yl = y > 0 ? y - 1 : 0, yr = y < H - 1 ? y + 1 : H - 1;
-        float gx = 0.0f, gy = 0.0f;
-        if (xr > xl) {
-            float den = __fmul_rn(cs, (float)(xr - xl));
-            gx = __fdiv_rn(__fsub_rn(__ldg(h + (int64_t)y * W + xr), __ldg(h + (int64_t)y * W + xl)), den);
+    const uint32_t runs = (uint32_t)((W + 3) >> 2);
+    const uint32_t items = runs * (uint32_t)H;
+    const float den1 = cs, den2 = __fmul_rn(cs, 2.0f);
+    for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
+        const int y = (int)(it / runs);
+        const int x0 = (int)(it - (uint32_t)y * runs) * 4;
+        const int yl = y > 0 ? y - 1 : 0, yr = y < H - 1 ? y + 1 : H - 1;
+        const float deny = yr - yl == 2 ? den2 : den1;
+        const int64_t row = (int64_t)y * W;
+        if (vec4) {
+            const float4 c = __ldg(reinterpret_cast<const float4*>(h + row + x0));
+            const float4 up = __ldg(reinterpret_cast<const float4*>(h + (int64_t)yl * W + x0));
+            const float4 dn = __ldg(reinterpret_cast<const float4*>(h + (int64_t)yr * W + x0));
+            const float left = x0 > 0 ? __ldg(h + row + x0 - 1) : c.x;
+            const float right = x0 + 4 < W ? __ldg(h + row + x0 + 4) : c.w;
+            const float hc[6] = {left, c.x, c.y, c.z, c.w, right};
+            const float hu[4] = {up.x, up.y, up.z, up.w}, hd[4] = {dn.x, dn.y, dn.z, dn.w};
+            float o_nx[4], o_ny[4], o_nz[4], o_t2[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int x = x0 + k;
+                const int xl = x > 0 ? x - 1 : 0, xr = x < W - 1 ? x + 1 : W - 1;
+                float gx = 0.0f, gy = 0.0f;
+                const float h_r = x < W - 1 ? hc[k + 2] : hc[k + 1];
+                const float h_l = x > 0 ? hc[k] : hc[k + 1];
+                if (xr > xl) gx = __fdiv_rn(__fsub_rn(h_r, h_l), xr - xl == 2 ? den2 : den1);
+                if (yr > yl) gy = __fdiv_rn(__fsub_rn(hd[k], hu[k]), deny);
+                normal_of(gx, gy, o_nx[k], o_ny[k], o_nz[k], o_t2[k]);
+            }
+            if (nrm) {
+                *reinterpret_cast<float4*>(nrm + row + x0) = make_float4(o_nx[0], o_nx[1], o_nx[2], o_nx[3]);
+                *reinterpret_cast<float4*>(nrm + plane + row + x0) = make_float4(o_ny[0], o_ny[1], o_ny[2], o_ny[3]);
+                *reinterpret_cast<float4*>(nrm + 2 * plane + row + x0) =
+                    make_float4(o_nz[0], o_nz[1], o_nz[2], o_nz[3]);
+            }
+            if (tan2) *reinterpret_cast<float4*>(tan2 + row + x0) = make_float4(o_t2[0], o_t2[1], o_t2[2], o_t2[3]);
+            if (slope_deg)
+                *reinterpret_cast<float4*>(slope_deg + row + x0) =
+                    make_float4(slope_deg_of(o_t2[0]), slope_deg_of(o_t2[1]), slope_deg_of(o_t2[2]),
+                                slope_deg_of(o_t2[3]));
+        } else {
+            const int x_end = x0 + 4 < W ? x0 + 4 : W;
+            for (int x = x0; x < x_end; ++x) {
+                const int xl = x > 0 ? x - 1 : 0, xr = x < W - 1 ? x + 1 : W - 1;
+                float gx = 0.0f, gy = 0.0f;
+                if (xr > xl) gx = __fdiv_rn(__fsub_rn(__ldg(h + row + xr), __ldg(h + row + xl)),
+                                           xr - xl == 2 ? den2 : den1);
+                if (yr > yl) gy = __fdiv_rn(__fsub_rn(__ldg(h + (int64_t)yr * W + x), __ldg(h + (int64_t)yl * W + x)),
+                                           deny);
+                float nx, ny, nz, t2;
+                normal_of(gx, gy, nx, ny, nz, t2);
+                const int64_t i = row + x;
+                if (nrm) {
+                    nrm[i] = nx;
+                    nrm[plane + i] = ny;
+                    nrm[2 * plane + i] = nz;
+                }
+                if (tan2) tan2[i] = t2;
+                if (slope_deg) slope_deg[i] = slope_deg_of(t2);
+            }
         }
-        if (yr > yl) {
-            float den = __fmul_rn(cs, (float)(yr - yl));
-            gy = __fdiv_rn(__fsub_rn(__ldg(h + (int64_t)yr * W + x), __ldg(h + (int64_t)yl * W + x)), den);
-        }
-        float t2 = __fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy));
-        if (nrm) {
-            float inv = __frcp_rn(__fsqrt_rn(__fadd_rn(t2, 1.0f)));
-            nrm[i] = __fmul_rn(-gx, inv);
-            nrm[plane + i] = __fmul_rn(-gy, inv);
-            nrm[2 * plane + i] = inv;
-        }
-        if (tan2) tan2[i] = t2;
-        if (slope_deg) slope_deg[i] = atanf(sqrtf(t2)) * 57.295779513082320876f;
     }
 }
 
@@ -114,33 +176,91 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* total)
     return base + incl - v;
 }
 
+// Selection bits of the RT_CELLS consecutive cells from `base` (bit k: cell
+// base + k is in [t_lo, t_hi]; cells past n are not).  Full, 16-byte-aligned
+// runs load as four float4.
+__device__ __forceinline__ uint32_t select_bits(const float* __restrict__ tan2, int64_t base, int64_t n, float t_lo,
+                                                float t_hi)
+{
+    uint32_t bits = 0u;
+    if (base + RT_CELLS <= n && (((uintptr_t)(tan2 + base)) & 15u) == 0) {
+        const float4* p = reinterpret_cast<const float4*>(tan2 + base);
+#pragma unroll
+        for (int q = 0; q < RT_CELLS / 4; ++q) {
+            const float4 t = __ldg(p + q);
+            bits |= ((t_lo <= t.x && t.x <= t_hi) ? 1u : 0u) << (4 * q);
+            bits |= ((t_lo <= t.y && t.y <= t_hi) ? 1u : 0u) << (4 * q + 1);
+            bits |= ((t_lo <= t.z && t.z <= t_hi) ? 1u : 0u) << (4 * q + 2);
+            bits |= ((t_lo <= t.w && t.w <= t_hi) ? 1u : 0u) << (4 * q + 3);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < RT_CELLS; ++k) {
+            if (base + k < n) {
+                const float t = __ldg(tan2 + base + k);
+                if (t_lo <= t && t <= t_hi) bits |= 1u << k;
+            }
+        }
+    }
+    return bits;
+}
+
+// Bits of the non-zero bytes among the RT_CELLS mask bytes from `base`.
+__device__ __forceinline__ uint32_t mask_bits(const uint8_t* __restrict__ mask, int64_t base, int64_t n)
+{
+    uint32_t bits = 0u;
+    if (base + RT_CELLS <= n && (((uintptr_t)(mask + base)) & 15u) == 0) {
+        const uint4 m = __ldg(reinterpret_cast<const uint4*>(mask + base));
+        const uint32_t w[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+        for (int k = 0; k < RT_CELLS; ++k) bits |= (((w[k >> 2] >> (8 * (k & 3))) & 0xffu) != 0u ? 1u : 0u) << k;
+    } else {
+#pragma unroll
+        for (int k = 0; k < RT_CELLS; ++k)
+            if (base + k < n && __ldg(mask + base + k) != 0) bits |= 1u << k;
+    }
+    return bits;
+}
+
+// Writes the selection bits as 0/1 bytes (one uint4 when full and aligned).
+__device__ __forceinline__ void store_mask(uint8_t* __restrict__ mask, int64_t base, int64_t n, uint32_t bits)
+{
+    uint32_t packed[RT_CELLS / 4];
+#pragma unroll
+    for (int q = 0; q < RT_CELLS / 4; ++q)
+        packed[q] = ((bits >> (4 * q)) & 1u) | (((bits >> (4 * q + 1)) & 1u) << 8) |
+                    (((bits >> (4 * q + 2)) & 1u) << 16) | (((bits >> (4 * q + 3)) & 1u) << 24);
+    if (base + RT_CELLS <= n && (((uintptr_t)(mask + base)) & 15u) == 0) {
+        *reinterpret_cast<uint4*>(mask + base) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    } else {
+        for (int k = 0; k < RT_CELLS; ++k)
+            if (base + k < n) mask[base + k] = (uint8_t)((bits >> k) & 1u);
+    }
+}
+
+// Ordered scatter of the selected indices of this thread's run, after the
+// block's exclusive scan of the per-thread counts.
+__device__ __forceinline__ void scatter_bits(uint32_t bits, int64_t base, const uint32_t* __restrict__ tile_offset,
+                                            uint32_t* __restrict__ cells)
+{
+    int total;
+    int off = block_exclusive_scan(__popc(bits), &total) + (int)tile_offset[blockIdx.x];
+    while (bits) {
+        const int k = __ffs(bits) - 1;
+        bits &= bits - 1;
+        cells[off++] = (uint32_t)(base + k);
+    }
+}
+
 __global__ void __launch_bounds__(RT_THREADS) k_release_mask(const float* __restrict__ tan2, int64_t n, float t_lo,
                                                              float t_hi, uint8_t* __restrict__ mask,
                                                              uint32_t* __restrict__ tile_count)
 {
     const int64_t base = (int64_t)blockIdx.x * RT_TILE + (int64_t)threadIdx.x * RT_CELLS;
-    int cnt = 0;
-    uint32_t packed[RT_CELLS / 4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-    for (int k = 0; k < RT_CELLS; ++k) {
-        int64_t i = base + k;
-        if (i < n) {
-            float t = __ldg(tan2 + i);
-            uint32_t sel = (t_lo <= t && t <= t_hi) ? 1u : 0u;
-            cnt += (int)sel;
-            packed[k >> 2] |= sel << (8 * (k & 3));
-        }
-    }
-    if (mask) {
-        if (base + RT_CELLS <= n && (((uintptr_t)(mask + base)) & 15u) == 0) {
-            *reinterpret_cast<uint4*>(mask + base) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-        } else {
-            for (int k = 0; k < RT_CELLS; ++k)
-                if (base + k < n) mask[base + k] = (uint8_t)((packed[k >> 2] >> (8 * (k & 3))) & 0xffu);
-        }
-    }
+    const uint32_t bits = select_bits(tan2, base, n, t_lo, t_hi);
+    if (mask) store_mask(mask, base, n, bits);
     int total;
-    block_exclusive_scan(cnt, &total);
+    block_exclusive_scan(__popc(bits), &total);
     if (threadIdx.x == 0) tile_count[blockIdx.x] = (uint32_t)total;
 }
 
@@ -168,37 +288,19 @@ __global__ void __launch_bounds__(RT_THREADS) k_release_scatter(const float* __r
                                                                 uint32_t* __restrict__ cells)
 {
     const int64_t base = (int64_t)blockIdx.x * RT_TILE + (int64_t)threadIdx.x * RT_CELLS;
-    uint32_t bits = 0;
-#pragma unroll
-    for (int k = 0; k < RT_CELLS; ++k) {
-        int64_t i = base + k;
-        if (i < n) {
-            float t = __ldg(tan2 + i);
-            if (t_lo <= t && t <= t_hi) bits |= 1u << k;
-        }
-    }
-    int total;
-    int off = block_exclusive_scan(__popc(bits), &total) + (int)tile_offset[blockIdx.x];
-    while (bits) {
-        int k = __ffs(bits) - 1;
-        bits &= bits - 1;
-        cells[off++] = (uint32_t)(base + k);
-    }
+    scatter_bits(select_bits(tan2, base, n, t_lo, t_hi), base, tile_offset, cells);
 }
 
-// Release cells given by a caller's mask (known release areas, Sec. 5.2:
-// "known release points encoded in a pre-computed texture"): per-tile counts
-// and ordered scatter of the cells whose mask byte is non-zero.
+// Release cells given by a mask -- a caller's (known release areas, Sec. 5.2:
+// "known release points encoded in a pre-computed texture") or the one the
+// first release pass wrote: per-tile counts and ordered scatter of the cells
+// whose mask byte is non-zero.
 __global__ void __launch_bounds__(RT_THREADS) k_mask_count(const uint8_t* __restrict__ mask, int64_t n,
                                                            uint32_t* __restrict__ tile_count)
 {
     const int64_t base = (int64_t)blockIdx.x * RT_TILE + (int64_t)threadIdx.x * RT_CELLS;
-    int cnt = 0;
-#pragma unroll
-    for (int k = 0; k < RT_CELLS; ++k)
-        if (base + k < n) cnt += __ldg(mask + base + k) != 0 ? 1 : 0;
     int total;
-    block_exclusive_scan(cnt, &total);
+    block_exclusive_scan(__popc(mask_bits(mask, base, n)), &total);
     if (threadIdx.x == 0) tile_count[blockIdx.x] = (uint32_t)total;
 }
 
@@ -207,17 +309,7 @@ __global__ void __launch_bounds__(RT_THREADS) k_mask_scatter(const uint8_t* __re
                                                              uint32_t* __restrict__ cells)
 {
     const int64_t base = (int64_t)blockIdx.x * RT_TILE + (int64_t)threadIdx.x * RT_CELLS;
-    uint32_t bits = 0;
-#pragma unroll
-    for (int k = 0; k < RT_CELLS; ++k)
-        if (base + k < n && __ldg(mask + base + k) != 0) bits |= 1u << k;
-    int total;
-    int off = block_exclusive_scan(__popc(bits), &total) + (int)tile_offset[blockIdx.x];
-    while (bits) {
-        int k = __ffs(bits) - 1;
-        bits &= bits - 1;
-        cells[off++] = (uint32_t)(base + k);
-    }
+    scatter_bits(mask_bits(mask, base, n), base, tile_offset, cells);
 }
 
 // Release points on a texture at 2^r times the DEM resolution
@@ -244,26 +336,32 @@ __global__ void __launch_bounds__(RT_THREADS) k_release_texture_mask(const float
         a = (uint32_t)(base - (int64_t)b * Wr);
     }
     float v = texel_centre(b, scale, hm1);
-    int cnt = 0;
-    uint32_t packed[RT_CELLS / 4] = {0u, 0u, 0u, 0u};
-#pragma unroll 4
+    uint32_t bits = 0u;
+    // footprint of the previous texel: on a finer texture 2^r consecutive
+    // texels share one, so its four values are loaded once
+    int o_prev = -1;
+    float t00 = 0.0f, t10 = 0.0f, t01 = 0.0f, t11 = 0.0f;
+#pragma unroll
     for (int k = 0; k < RT_CELLS; ++k) {
         if (base + k < n) {
             const float u = texel_centre(a, scale, wm1);
             const int i0 = __float2int_rd(u), j0 = __float2int_rd(v);
             const float fx = __fsub_rn(u, __int2float_rn(i0)), fy = __fsub_rn(v, __int2float_rn(j0));
-            const int di = i0 + 1 < W ? 1 : 0;
-            const int dj = j0 + 1 < H ? W : 0;
             const int o = j0 * W + i0;
-            const float t00 = __ldg(tan2 + o), t10 = __ldg(tan2 + o + di);
-            const float t01 = __ldg(tan2 + o + dj), t11 = __ldg(tan2 + o + dj + di);
+            if (o != o_prev) {
+                const int di = i0 + 1 < W ? 1 : 0;
+                const int dj = j0 + 1 < H ? W : 0;
+                t00 = __ldg(tan2 + o);
+                t10 = __ldg(tan2 + o + di);
+                t01 = __ldg(tan2 + o + dj);
+                t11 = __ldg(tan2 + o + dj + di);
+                o_prev = o;
+            }
             const float ox = __fsub_rn(1.0f, fx), oy = __fsub_rn(1.0f, fy);
             const float top = __fadd_rn(__fmul_rn(t00, ox), __fmul_rn(t10, fx));
             const float bot = __fadd_rn(__fmul_rn(t01, ox), __fmul_rn(t11, fx));
             const float T = __fadd_rn(__fmul_rn(top, oy), __fmul_rn(bot, fy));
-            const uint32_t sel = (t_lo <= T && T <= t_hi) ? 1u : 0u;
-            cnt += (int)sel;
-            packed[k >> 2] |= sel << (8 * (k & 3));
+            bits |= ((t_lo <= T && T <= t_hi) ? 1u : 0u) << k;
             if (++a == Wr) {
                 a = 0u;
                 ++b;
@@ -271,14 +369,9 @@ __global__ void __launch_bounds__(RT_THREADS) k_release_texture_mask(const float
             }
         }
     }
-    if (base + RT_CELLS <= n && (((uintptr_t)(mask + base)) & 15u) == 0) {
-        *reinterpret_cast<uint4*>(mask + base) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-    } else {
-        for (int k = 0; k < RT_CELLS; ++k)
-            if (base + k < n) mask[base + k] = (uint8_t)((packed[k >> 2] >> (8 * (k & 3))) & 0xffu);
-    }
+    store_mask(mask, base, n, bits);
     int total;
-    block_exclusive_scan(cnt, &total);
+    block_exclusive_scan(__popc(bits), &total);
     if (threadIdx.x == 0) tile_count[blockIdx.x] = (uint32_t)total;
 }
 
@@ -312,7 +405,8 @@ extern "C" awo_status awo_decode_u16(const uint16_t* d_q, awo_grid g, float scal
 {
     if (!d_q || !d_h || !grid_ok(g) || !(scale > 0.0f) || !(scale < 3.0e38f)) return AWO_EINVAL;
     const int64_t n = cells_of(g);
-    k_decode_u16<<<stream_blocks(n, 256), 256, 0, as_stream(stream)>>>(d_q, n, scale, d_h);
+    const bool vec4 = (((uintptr_t)d_q) & 7u) == 0 && (((uintptr_t)d_h) & 15u) == 0;
+    k_decode_u16<<<stream_blocks(vec4 ? n / 4 + 1 : n, 256), 256, 0, as_stream(stream)>>>(d_q, n, scale, d_h, vec4);
     return launch_status();
 }
 
@@ -321,9 +415,11 @@ extern "C" awo_status awo_normals(const float* d_h, awo_grid g, float* d_normal,
 {
     if (!d_h || !grid_ok(g)) return AWO_EINVAL;
     if (!d_normal && !d_tan2 && !d_slope_deg) return AWO_OK;
-    const int64_t n = cells_of(g);
-    k_normals<<<stream_blocks(n, 256), 256, 0, as_stream(stream)>>>(d_h, g.width, g.height, g.cell_size, d_normal,
-                                                                     d_tan2, d_slope_deg);
+    const int64_t items = (int64_t)((g.width + 3) / 4) * g.height;
+    auto a16 = [](const void* p) { return p == nullptr || (((uintptr_t)p) & 15u) == 0; };
+    const bool vec4 = (g.width % 4) == 0 && a16(d_h) && a16(d_normal) && a16(d_tan2) && a16(d_slope_deg);
+    k_normals<<<stream_blocks(items, 256), 256, 0, as_stream(stream)>>>(d_h, g.width, g.height, g.cell_size,
+                                                                         d_normal, d_tan2, d_slope_deg, vec4);
     return launch_status();
 }
 
@@ -350,7 +446,10 @@ extern "C" awo_status awo_release(const float* d_tan2, awo_grid g, double slope_
     cudaStream_t s = as_stream(stream);
     k_release_mask<<<tiles, RT_THREADS, 0, s>>>(d_tan2, n, t_lo, t_hi, d_mask, tile_count);
     k_release_scan<<<1, 1024, 0, s>>>(tile_count, tiles, tile_offset, d_n);
-    k_release_scatter<<<tiles, RT_THREADS, 0, s>>>(d_tan2, n, t_lo, t_hi, tile_offset, d_cells);
+    if (d_mask)  // 1 byte per cell instead of 4
+        k_mask_scatter<<<tiles, RT_THREADS, 0, s>>>(d_mask, n, tile_offset, d_cells);
+    else
+        k_release_scatter<<<tiles, RT_THREADS, 0, s>>>(d_tan2, n, t_lo, t_hi, tile_offset, d_cells);
     return launch_status();
 }
 
@@ -407,7 +506,10 @@ extern "C" awo_status awo_release_noalloc(const float* d_tan2, awo_grid g, doubl
     cudaStream_t s = as_stream(stream);
     k_release_mask<<<tiles, RT_THREADS, 0, s>>>(d_tan2, n, t_lo, t_hi, d_mask, tile_count);
     k_release_scan<<<1, 1024, 0, s>>>(tile_count, tiles, tile_offset, d_n);
-    k_release_scatter<<<tiles, RT_THREADS, 0, s>>>(d_tan2, n, t_lo, t_hi, tile_offset, d_cells);
+    if (d_mask)  // 1 byte per cell instead of 4
+        k_mask_scatter<<<tiles, RT_THREADS, 0, s>>>(d_mask, n, tile_offset, d_cells);
+    else
+        k_release_scatter<<<tiles, RT_THREADS, 0, s>>>(d_tan2, n, t_lo, t_hi, tile_offset, d_cells);
     return launch_status();
 }
 
