@@ -312,7 +312,8 @@ def run_awo(args, R: Ranks):
     torch.cuda.synchronize()
     st = ov.stats_dict()
     visits = st["total_steps"] + st["n_traj"]
-    launches_per_step = (1 if w.quantised else 0) + 1 + 3 + 1 + 1 + max(w.lod_levels - 1, 0)
+    # decode, normals, release (mask, scan, scatter), particle prologue and kernel, finalize, mipmap levels
+    launches_per_step = (1 if w.quantised else 0) + 1 + 3 + 2 + 1 + max(w.lod_levels - 1, 0)
 
     peaks_probe = _probe_peaks(torch, awo)
     clocks = ClockSampler(R.local)
