@@ -335,7 +335,11 @@ __global__ void __launch_bounds__(RT_THREADS) k_release_texture_mask(const float
         b = (uint32_t)(base / Wr);
         a = (uint32_t)(base - (int64_t)b * Wr);
     }
+    // row terms, recomputed when the run wraps to the next texture row
     float v = texel_centre(b, scale, hm1);
+    int j0 = __float2int_rd(v);
+    float fy = __fsub_rn(v, __int2float_rn(j0)), oy = __fsub_rn(1.0f, fy);
+    int row = j0 * W, dj = j0 + 1 < H ? W : 0;
     uint32_t bits = 0u;
     // footprint of the previous texel: on a finer texture 2^r consecutive
     // texels share one, so its four values are loaded once
@@ -345,19 +349,18 @@ __global__ void __launch_bounds__(RT_THREADS) k_release_texture_mask(const float
     for (int k = 0; k < RT_CELLS; ++k) {
         if (base + k < n) {
             const float u = texel_centre(a, scale, wm1);
-            const int i0 = __float2int_rd(u), j0 = __float2int_rd(v);
-            const float fx = __fsub_rn(u, __int2float_rn(i0)), fy = __fsub_rn(v, __int2float_rn(j0));
-            const int o = j0 * W + i0;
+            const int i0 = __float2int_rd(u);
+            const float fx = __fsub_rn(u, __int2float_rn(i0));
+            const int o = row + i0;
             if (o != o_prev) {
                 const int di = i0 + 1 < W ? 1 : 0;
-                const int dj = j0 + 1 < H ? W : 0;
                 t00 = __ldg(tan2 + o);
                 t10 = __ldg(tan2 + o + di);
                 t01 = __ldg(tan2 + o + dj);
                 t11 = __ldg(tan2 + o + dj + di);
                 o_prev = o;
             }
-            const float ox = __fsub_rn(1.0f, fx), oy = __fsub_rn(1.0f, fy);
+            const float ox = __fsub_rn(1.0f, fx);
             const float top = __fadd_rn(__fmul_rn(t00, ox), __fmul_rn(t10, fx));
             const float bot = __fadd_rn(__fmul_rn(t01, ox), __fmul_rn(t11, fx));
             const float T = __fadd_rn(__fmul_rn(top, oy), __fmul_rn(bot, fy));
@@ -366,6 +369,11 @@ __global__ void __launch_bounds__(RT_THREADS) k_release_texture_mask(const float
                 a = 0u;
                 ++b;
                 v = texel_centre(b, scale, hm1);
+                j0 = __float2int_rd(v);
+                fy = __fsub_rn(v, __int2float_rn(j0));
+                oy = __fsub_rn(1.0f, fy);
+                row = j0 * W;
+                dj = j0 + 1 < H ? W : 0;
             }
         }
     }
