@@ -53,7 +53,7 @@ ALG_OPS_PER_VISIT = 176
 # read + write of a 6144^2 crop launch, divided by its visits), keyed by the
 # SHA-256 prefix of the kernel source it was taken on; a changed kernel
 # reports traffic null until it is captured again.
-DRAM_BYTES_PER_VISIT: dict[str, float] = {"00f893967c991e6e": (268.306688e6 + 55.044864e6) / 1754008332}
+DRAM_BYTES_PER_VISIT: dict[str, float] = {"46a1b03b4c8b1fa7": (268.26496e6 + 54.791936e6) / 1754008332}
 
 
 def _args():

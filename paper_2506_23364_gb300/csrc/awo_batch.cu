@@ -57,6 +57,7 @@ struct BatchHeader {
     unsigned long long stats[AWO_BATCH_MAX][6];
 };
 constexpr size_t BATCH_HEADER_BYTES = ((sizeof(BatchHeader) + 255) / 256) * 256;
+constexpr uint32_t BATCH_REFILL_IDLE = 12;
 
 static_assert(sizeof(awo_sim_request) == 112, "awo_sim_request layout (C ABI)");
 static_assert(offsetof(awo_sim_request, params) == 48, "awo_sim_request layout (C ABI)");
@@ -217,6 +218,7 @@ __global__ void __launch_bounds__(THREADS) k_batch_simulate(const __grid_constan
     uint32_t cur_ci = 0u, cur_j = 0u;
     bool exhausted = (total_chunks == 0ull);
     bool have_p = false;  // fetched chunk waiting for the warp to drain
+    uint32_t idle_acc = 0u;  // idle lane-iterations since the last lane refill (warp-uniform)
     int p_r = 0;
     unsigned long long p_t = 0ull, p_end = 0ull;
 
@@ -224,7 +226,12 @@ __global__ void __launch_bounds__(THREADS) k_batch_simulate(const __grid_constan
 
     while (true) {
         const unsigned idle = __ballot_sync(0xffffffffu, !live);
-        const bool can_refill = idle != 0u && (!WARP_REFILL || idle == 0xffffffffu);
+        idle_acc += (uint32_t)__popc(idle);
+        // lane refill waits for BATCH_REFILL_IDLE idle lane-iterations (as in
+        // the single-request kernel); warp refill for all 32 lanes
+        const bool can_refill =
+            idle != 0u && (WARP_REFILL ? idle == 0xffffffffu : idle_acc >= BATCH_REFILL_IDLE);
+        if (can_refill) idle_acc = 0u;
         if (can_refill && cur_t >= end_t && !exhausted && !have_p) {
             unsigned long long g = 0;
             if (lane == 0) g = atomicAdd(&a.hdr->next_chunk, 1ull);
