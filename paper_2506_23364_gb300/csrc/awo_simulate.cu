@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(SIM_THREADS) k_simulate(const __grid_constant_
     AWO_LANE_STATE
 
     while (true) {
-        // ---- refill idle lanes (one round per move) ------------------------
+        // ---- refill idle lanes (once they add up to SIM_REFILL_IDLE) --------
         const unsigned idle = __ballot_sync(0xffffffffu, !live);
         idle_acc += (uint32_t)__popc(idle);
         if (idle != 0u && idle_acc >= SIM_REFILL_IDLE && !exhausted) {
