@@ -54,7 +54,7 @@ ALG_OPS_PER_VISIT = 176
 # read + write of a 6144^2 crop launch, divided by its visits), keyed by the
 # SHA-256 prefix of the kernel's code (comments removed) it was taken on; a
 # changed kernel reports traffic null until it is captured again.
-DRAM_BYTES_PER_VISIT: dict[str, float] = {"95111a83b58d210a": (268.26496e6 + 54.791936e6) / 1754008332}
+DRAM_BYTES_PER_VISIT: dict[str, float] = {"ba64dc42115c0e0b": (269.251584e6 + 55.013376e6) / 1754008332}
 
 
 def _args():

@@ -30,7 +30,7 @@
 namespace awo {
 
 struct BatchReq {
-    // request constants (names read by AWO_MOVE_ONCE)
+    // request constants (names read by AWO_MOVE_WORDS)
     const float* h;
     uint32_t* count;
     float* maxe;
@@ -291,9 +291,9 @@ __global__ void __launch_bounds__(THREADS) k_batch_simulate(const __grid_constan
             continue;
         }
         if (TABLE_KEYS)
-            AWO_MOVE_ONCE(q, a.keys);
+            AWO_MOVE_PAIR(q, a.keys);
         else
-            AWO_MOVE_ONCE(q, (KeysWeyl{q.k0, q.k1}));
+            AWO_MOVE_PAIR(q, (KeysWeyl{q.k0, q.k1}));
     }
     if (cr >= 0) AWO_FLUSH_COUNTERS(a.hdr->stats[cr]);
 }

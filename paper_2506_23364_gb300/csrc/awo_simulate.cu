@@ -13,16 +13,18 @@
 //    warps of the GPU, touch a compact region of the DEM and of the rasters,
 //    which stays L2-resident even when the DEM does not.
 //  * One integer division per chunk and none per particle: the cursor
-//    carries (cell, j), and a cell index becomes (x, y) through a float
-//    reciprocal of W and one exact correction step.
+//    carries (release-list entry, j), and the start record holds the cell's
+//    coordinates.
 //  * A particle starts at refill time from the 16-byte start record of its
 //    release cell (position, height, first direction), written by a prologue
 //    kernel that also records the release visits of all N particles of the
-//    cell with one reduction.  Each loop iteration is then exactly one
-//    move and its visit -- direction from the footprint kept in registers,
-//    draw, step, footprint and energy at the new position, record -- written
-//    without data-dependent branches (selects and predicated reductions), so
-//    a warp runs one instruction stream.
+//    cell with one reduction.  Each loop iteration is then two moves and
+//    their visits from one Philox block (moves n and n + 1 take words 0-1 and
+//    2-3 of block n >> 1; live lanes are always at an even n there) --
+//    direction from the footprint kept in registers, step, footprint and
+//    energy at the new position, record -- written without data-dependent
+//    branches (selects and predicated reductions), so a warp runs one
+//    instruction stream.
 //  * Visits go to the rasters as fire-and-forget reductions (RED.ADD on the
 //    count, RED.MAX on the bits of the non-negative energy), one pair per
 //    lane: measured on GB300, merging the lanes of a warp that hit the same
@@ -47,7 +49,7 @@ struct SimWorkspace {
 static_assert(sizeof(SimWorkspace) == 64, "workspace layout");
 
 struct SimArgs {
-    // request constants (names read by AWO_MOVE_ONCE)
+    // request constants (names read by AWO_MOVE_WORDS)
     const float* h;
     uint32_t* count;
     float* maxe;
@@ -186,7 +188,7 @@ __global__ void __launch_bounds__(SIM_THREADS) k_simulate(const __grid_constant_
             if (exhausted) break;
             continue;
         }
-        AWO_MOVE_ONCE(a, a.keys);
+        AWO_MOVE_PAIR(a, a.keys);
     }
     AWO_FLUSH_COUNTERS(a.ws->stats);
 }

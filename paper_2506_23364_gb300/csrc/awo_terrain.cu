@@ -328,12 +328,14 @@ __global__ void __launch_bounds__(RT_THREADS) k_release_texture_mask(const float
                                                                      uint8_t* __restrict__ mask,
                                                                      uint32_t* __restrict__ tile_count)
 {
-    const int64_t base = (int64_t)blockIdx.x * RT_TILE + (int64_t)threadIdx.x * RT_CELLS;
+    // the texture has fewer than 2^31 texels: 32-bit indices throughout
+    const uint32_t base = blockIdx.x * (uint32_t)RT_TILE + threadIdx.x * (uint32_t)RT_CELLS;
+    const uint32_t n32 = (uint32_t)n;
     const float wm1 = __int2float_rn(W - 1), hm1 = __int2float_rn(H - 1);
     uint32_t b = 0u, a = 0u;
-    if (base < n) {
-        b = (uint32_t)(base / Wr);
-        a = (uint32_t)(base - (int64_t)b * Wr);
+    if (base < n32) {
+        b = base / Wr;
+        a = base - b * Wr;
     }
     // row terms, recomputed when the run wraps to the next texture row
     float v = texel_centre(b, scale, hm1);
@@ -347,7 +349,7 @@ __global__ void __launch_bounds__(RT_THREADS) k_release_texture_mask(const float
     float t00 = 0.0f, t10 = 0.0f, t01 = 0.0f, t11 = 0.0f;
 #pragma unroll
     for (int k = 0; k < RT_CELLS; ++k) {
-        if (base + k < n) {
+        if (base + k < n32) {
             const float u = texel_centre(a, scale, wm1);
             const int i0 = __float2int_rd(u);
             const float fx = __fsub_rn(u, __int2float_rn(i0));
