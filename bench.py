@@ -44,11 +44,12 @@ UNIT = "trajectory-steps/s"
 ALG_BYTES_PER_VISIT = 24
 
 # Algorithmic lane operations per visit of the particle kernel, counted from
-# the formulas of the move: one Philox4x32-10 block (10 rounds x (2 multiply
-# high + 2 multiply low + 4 xor + 2 key add) = 100) and two uniforms (8);
-# bilinear height 11; gradient and its normalisation 17; direction 17; move
-# and domain test 8; energy and stop test 6; visited cell 5; floors 4.
-ALG_OPS_PER_VISIT = 176
+# the formulas of the move: half a Philox4x32-10 block (a block -- 10 rounds
+# x (2 multiply high + 2 multiply low + 4 xor + 2 key add) = 100 -- yields
+# the four words of two moves) = 50, and the move's two uniforms 8; bilinear
+# height 11; gradient and its normalisation 17; direction 17; move and
+# domain test 8; energy and stop test 6; visited cell 5; floors 4.
+ALG_OPS_PER_VISIT = 126
 
 # DRAM bytes per visit of the particle kernel from an ncu capture (dram__bytes
 # read + write of a 6144^2 crop launch, divided by its visits), keyed by the
