@@ -87,6 +87,10 @@ __device__ __forceinline__ void soft_particle(const SoftArgs& a, uint32_t ci, ui
     long long Q = 0;
     float tmu = 0.f, tk = 0.f, smu = 0.f, sk = 0.f, acc_mu = 0.f, acc_k = 0.f, acc_w = 0.f;
     uint32_t n = 0;
+    // the Philox block of moves n and n + 1 (words 0-1, then 2-3): computed at
+    // even n only; the lanes of a warp start their particles together and
+    // step in lock-step, so the branch is uniform across active lanes
+    uint4 r = make_uint4(0u, 0u, 0u, 0u);
     while (n < a.max_steps) {
         const float ox = __fsub_rn(1.0f, fx), oy = __fsub_rn(1.0f, fy);
         const float ga = __fadd_rn(__fmul_rn(__fsub_rn(h10, h00), oy), __fmul_rn(__fsub_rn(h11, h01), fy));
@@ -98,8 +102,8 @@ __device__ __forceinline__ void soft_particle(const SoftArgs& a, uint32_t ci, ui
             gx = __fmul_rn(-ga, ginv);
             gy = __fmul_rn(-gb, ginv);
         }
-        const uint4 r = philox4x32_10(make_uint4(cell, j, n >> 1, 0u), a.keys);
         const bool odd = (n & 1u) != 0u;
+        if (!odd) r = philox4x32_10(make_uint4(cell, j, n >> 1, 0u), a.keys);
         const float xix = uniform_pm1(odd ? r.z : r.x);
         const float xiy = uniform_pm1(odd ? r.w : r.y);
         const float rx = __fadd_rn(__fadd_rn(__fmul_rn(a.P, dx), __fmul_rn(a.oneP, gx)), __fmul_rn(a.R, xix));
