@@ -16,7 +16,7 @@ import torch
 
 from . import (SimParams, SimRequest, Tuning, awo_simulate_batched, awo_simulate_batched_workspace_bytes,
                awo_tune_batched, sim_request, stats_dict)
-from .pipeline import SIM_CLEAR_OUTPUTS, Overlay
+from .pipeline import SIM_CLEAR_OUTPUTS, Overlay, _ranged
 
 
 def _per_region(x, n):
@@ -61,6 +61,7 @@ class Batch:
         for ov, (lo, hi), sc in zip(self.ovs, self.release_deg, self.decode_scale):
             ov.terrain(lo, hi, sc, stream)
 
+    @_ranged("awo simulate (batched)")
     def simulate(self, stream=None):
         awo_simulate_batched(self.reqs, self.ws, self.tuning, self.stats, stream)
 

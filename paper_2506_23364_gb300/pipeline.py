@@ -20,6 +20,21 @@ from . import (AWO_OK, Grid, SimParams, awo_decode_u16, awo_finalize, awo_normal
 SIM_CLEAR_OUTPUTS = 1
 
 
+def _ranged(name: str):
+    """Wraps a stage in an NVTX range (visible in a profiler's timeline)."""
+    def deco(fn):
+        def wrapped(*args, **kwargs):
+            torch.cuda.nvtx.range_push(name)
+            try:
+                return fn(*args, **kwargs)
+            finally:
+                torch.cuda.nvtx.range_pop()
+        wrapped.__doc__ = fn.__doc__
+        wrapped.__name__ = fn.__name__
+        return wrapped
+    return deco
+
+
 def _ws(nbytes: int, device) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 16) + 256, dtype=torch.uint8, device=device)
 
@@ -79,6 +94,7 @@ class Overlay:
             src = torch.from_numpy(np.ascontiguousarray(dem, dtype=np.float32)) if isinstance(dem, np.ndarray) else dem
             self.h.copy_(src, non_blocking=non_blocking)
 
+    @_ranged("awo terrain")
     def terrain(self, slope_lo_deg: float, slope_hi_deg: float, decode_scale: float = 0.1, stream=None):
         """a0-b: decode, normals and release (the count stays on the device)."""
         if self.quantised:
@@ -91,6 +107,7 @@ class Overlay:
             awo_release(self.tan2, self.g, slope_lo_deg, slope_hi_deg, self.mask, self.cells, self.n_rel,
                         self.ws_rel, stream)
 
+    @_ranged("awo terrain (mask)")
     def terrain_from_mask(self, mask: torch.Tensor, decode_scale: float = 0.1, stream=None):
         """a0-b': decode, normals and the release list from a caller's uint8
         mask (at the release texture's resolution)."""
@@ -99,6 +116,7 @@ class Overlay:
         awo_normals(self.h, self.g, self.normal, self.tan2, self.slope, stream)
         awo_release_from_mask(mask, self.g_rel, self.cells, self.n_rel, self.ws_rel, stream)
 
+    @_ranged("awo simulate")
     def simulate(self, params: SimParams, clear: bool = True, stream=None, cells=None, n_cells=None):
         """c: particles from the release list (or from the given cells)."""
         p = SimParams.from_buffer_copy(params)
@@ -112,6 +130,7 @@ class Overlay:
             awo_simulate(self.h, self.g, cells, None, int(n_cells), p, self.count, self.maxe, self.stats,
                          self.ws_sim, stream)
 
+    @_ranged("awo overlay")
     def overlay(self, gravity: float = 9.81, stream=None):
         """c'-d: velocity indicator and mipmap."""
         awo_finalize(self.maxe, self.g, gravity, self.vel, stream)
