@@ -277,8 +277,10 @@ typedef struct {
  *   group_particles:   particles a warp takes per fetch, 32 .. 65536 (0 = chosen
  *                      per launch: about all particles / (4 x the grid's warps),
  *                      rounded down to a multiple of 32, within 32 .. 1024)
- *   refill: AWO_REFILL_LANE -- a lane starts the next particle as soon as its
- *           particle ends (trajectory per thread, continuously refilled);
+ *   refill: AWO_REFILL_LANE -- ended lanes take the next particles while the
+ *           warp's other lanes keep moving, once the idle lanes add up to 12
+ *           idle lane-iterations (trajectory per thread, continuously
+ *           refilled);
  *           AWO_REFILL_WARP -- a warp starts 32 particles together and takes
  *           the next 32 only when all have ended (trajectories per warp, in
  *           lock-step batches). */
