@@ -70,6 +70,7 @@ def _args():
     ap.add_argument("--rate", type=float, default=200.0, help="Poisson arrival rate of the served workload (1/s)")
     ap.add_argument("--crop", type=int, default=0, help="use the top-left N x N crop of the workload's DEM")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-instances", type=int, default=3, help="workflow instances of the pipelined end-to-end run")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-threads", type=int, default=0, help="host threads of the oracle (0 = all cores)")
@@ -399,23 +400,26 @@ def _e2e(args, R, awo, w, ov, host_dem, run, steps_one, steps_all) -> dict:
     """The same workload end to end through the public API: every step copies
     its DEM from pinned host memory, runs the workflow and copies the whole
     overlay (count and velocity, every mipmap level) back to pinned host
-    memory.  Pipelined form (the value): two workflow instances on two CUDA
-    streams take steps in turn, so the copies of one step overlap the kernels
-    of the next.  Serial form (reported beside it): one stream, each step
-    synchronised before the next."""
+    memory.  Pipelined form (the value): --e2e-instances workflow instances
+    (default 3) on as many CUDA streams take steps in turn, so the copies of
+    one step overlap the kernels of the next; 4 x --e2e-steps steps are timed
+    so that the unoverlapped first copy-in and last copy-out weigh little.
+    Serial form (reported beside it): one stream, each step synchronised
+    before the next."""
     import numpy as np
     import torch
 
     src = np.ascontiguousarray(host_dem).view(np.int16) if w.quantised else host_dem
     pin_dem = torch.from_numpy(src).pin_memory()
-    ov2 = awo.Overlay(w.width, w.height, w.cell_size, quantised=w.quantised, levels=w.lod_levels,
-                      device=R.device, want_slope=False, release_log2=ov.release_log2)
+    m = max(1, args.e2e_instances)
+    extra = [awo.Overlay(w.width, w.height, w.cell_size, quantised=w.quantised, levels=w.lod_levels,
+                         device=R.device, want_slope=False, release_log2=ov.release_log2) for _ in range(m - 1)]
 
     def outs_of(o):
         dev = [o.count, o.vel] + [t for pair in zip(o.count_lv, o.vel_lv) for t in pair]
         return [(d, torch.empty(d.shape, dtype=d.dtype).pin_memory()) for d in dev]
 
-    insts = [(ov, outs_of(ov), torch.cuda.Stream(R.device)), (ov2, outs_of(ov2), torch.cuda.Stream(R.device))]
+    insts = [(o, outs_of(o), torch.cuda.Stream(R.device)) for o in [ov] + extra]
     bi = pin_dem.numel() * pin_dem.element_size()
     bo = sum(h.numel() * h.element_size() for _, h in insts[0][1])
 
@@ -440,26 +444,28 @@ def _e2e(args, R, awo, w, ov, host_dem, run, steps_one, steps_all) -> dict:
         if k > 0:
             serial.append(a.elapsed_time(b))
     serial_ms = R.reduce(statistics.mean(serial), "max")
-    # pipelined: 2 instances on 2 streams, 2 * n steps after 2 warm-up steps
+    # pipelined: m instances on m streams, one warm-up step each, then 4 n steps
     for inst in insts:
         one(inst)
     torch.cuda.synchronize()
     R.barrier()
-    s0, s1 = insts[0][2], insts[1][2]
+    s0 = insts[0][2]
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(s0)
-    s1.wait_event(a)
-    k_steps = 2 * n
+    for inst in insts[1:]:
+        inst[2].wait_event(a)
+    k_steps = 4 * n
     for k in range(k_steps):
-        one(insts[k % 2])
-    s0.wait_stream(s1)
+        one(insts[k % m])
+    for inst in insts[1:]:
+        s0.wait_stream(inst[2])
     b.record(s0)
     b.synchronize()
     pipe_ms = R.reduce(a.elapsed_time(b) / k_steps, "max")
-    del ov2
+    del extra, insts
     return {"value": steps_all / (pipe_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": bi,
             "d2h_bytes_per_step": bo, "ms_per_step": pipe_ms, "steps": k_steps,
-            "form": "2 workflow instances on 2 CUDA streams, steps alternate (copies overlap the next step)",
+            "form": f"{m} workflow instances on {m} CUDA streams, steps in turn (copies overlap the next step)",
             "serial": {"value": steps_all / (serial_ms / 1e3), "ms_per_step": serial_ms, "steps": n,
                        "form": "1 stream, synchronised after every step"}}
 
