@@ -62,13 +62,21 @@ class OverlayRequest:
         """Device bytes the request's buffers take (see Overlay + batch workspace)."""
         H, W = self.dem.shape
         n = H * W
-        per_cell = (2 if self.quantised else 0) + 4 + 4 + 4 + 4 + 4 + 4 + 16  # q, h, tan2, cells, count, maxe, vel, starts
+        per_cell = (2 if self.quantised else 0) + 4 + 4 + 4 + 4 + 4  # q, h, tan2, count, maxe, vel
+        r = int(self.params.get("release_log2", 0))
+        if r >= 0:
+            entries = n << (2 * r)
+        else:
+            q = 1 << (-r)
+            entries = -(-W // q) * -(-H // q)
+        # release list (4 B) and start-record slot (32 B) per release entry, texture mask when r != 0
+        per_entry = 4 + 32 + (1 if r else 0)
         lv = 0
         h, w = H, W
         for _ in range(1, self.levels):
             h, w = (h + 1) // 2, (w + 1) // 2
             lv += 8 * h * w
-        return n * per_cell + lv + (64 << 10)
+        return n * per_cell + entries * per_entry + lv + (64 << 10)
 
 
 @dataclass

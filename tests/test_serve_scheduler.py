@@ -138,3 +138,15 @@ def test_scheduler_rejects_bad_configuration():
         Scheduler(0, 1, 1)
     with pytest.raises(ValueError):
         Scheduler(100, 1, 129)
+
+
+def test_device_bytes_counts_release_texture():
+    """The memory estimate grows with the release texture: a start-record
+    slot and a list entry per release texel, plus the texture mask."""
+    dem = np.zeros((64, 96), np.uint16)
+    b0 = OverlayRequest(dem, 10.0, (30.0, 45.0), {}).device_bytes()
+    b1 = OverlayRequest(dem, 10.0, (30.0, 45.0), {"release_log2": 1}).device_bytes()
+    bm = OverlayRequest(dem, 10.0, (30.0, 45.0), {"release_log2": -1}).device_bytes()
+    n = 64 * 96
+    assert b1 - b0 == 3 * n * 36 + 4 * n          # 3n more entries, and the 4n-byte mask
+    assert b0 - bm == n * 36 - (n // 4) * 37      # a quarter of the entries, with their mask
