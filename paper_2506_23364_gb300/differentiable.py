@@ -77,14 +77,15 @@ class SoftDeposit(torch.autograd.Function):
         D = prob.forward_raw(mu, k, w)
         ctx.prob, ctx.mu, ctx.k = prob, mu, k
         ctx.save_for_backward(w)
-        ctx.shapes = (log_mu, log_k)
+        ctx.meta = tuple((torch.as_tensor(t).shape, torch.as_tensor(t).dtype, torch.as_tensor(t).device)
+                         for t in (log_mu, log_k))
         return D
 
     @staticmethod
     def backward(ctx, gD):
         (w,) = ctx.saved_tensors
         gt, gw = ctx.prob.backward_raw(ctx.mu, ctx.k, w, gD)
-        lm, lk = ctx.shapes
-        g_mu = gt[0].to(device=lm.device, dtype=lm.dtype).reshape(lm.shape)
-        g_k = gt[1].to(device=lk.device, dtype=lk.dtype).reshape(lk.shape)
+        (sm, dm, vm), (sk, dk, vk) = ctx.meta
+        g_mu = gt[0].to(device=vm, dtype=dm).reshape(sm)
+        g_k = gt[1].to(device=vk, dtype=dk).reshape(sk)
         return g_mu, g_k, gw.to(torch.float32), None
