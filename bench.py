@@ -55,6 +55,10 @@ ALG_OPS_PER_VISIT = 126
 # read + write of a 6144^2 crop launch, divided by its visits), keyed by the
 # SHA-256 prefix of the kernel's code (comments removed) it was taken on; a
 # changed kernel reports traffic null until it is captured again.
+# L2 throughput of the same capture (lts__throughput.avg.pct_of_peak_sustained_elapsed
+# / 100): the particle kernel's share of the L2's own ceiling, keyed like the
+# traffic above.
+L2_THROUGHPUT_FRAC: dict[str, float] = {"ba64dc42115c0e0b": 0.60208951}
 DRAM_BYTES_PER_VISIT: dict[str, float] = {"ba64dc42115c0e0b": (269.251584e6 + 55.013376e6) / 1754008332}
 
 
@@ -374,6 +378,9 @@ def run_awo(args, R: Ranks):
     l2["gather_frac"] = l2["gather_loads_per_s"] / l2["probe_l2_gather_loads_per_s"]
     l2["red_frac"] = l2["red_per_s"] / l2["probe_l2_red_per_s"]
     l2["frac_of_binding"] = max(l2["gather_frac"], l2["red_frac"])
+    # the per-lane probes scatter every lane; the kernel's lanes share sectors,
+    # so its rates exceed them: the ncu L2 throughput is the tighter figure
+    l2["ncu_lts_throughput_frac"] = L2_THROUGHPUT_FRAC.get(sha)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": R.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True, "scaling": "weak",
