@@ -10,45 +10,45 @@
 
 namespace awo {
 
-__device__ __forceinline__ uint8_t to_u8(float x)
-{
-    if (!(x > 0.0f)) return 0;
-    if (x > 255.0f) return 255;
-    return (uint8_t)__float2uint_rn(x);
-}
+// Round half to even into [0, 255]: non-positive and NaN give 0, values
+// above 255 give 255 (the saturating conversion of fmaxf(x, 0), capped).
+__device__ __forceinline__ uint32_t to_u8(float x) { return min(__float2uint_rn(fmaxf(x, 0.0f)), 255u); }
 
-// The colour ramp in shared memory (stop values and colours as floats), so
-// that per-texel lookups with a data-dependent stop index stay on chip.
+// The colour ramp in shared memory: the stop values, and per segment k its
+// start value, width v[k+1] - v[k], start colour and colour step c[k+1] - c[k]
+// (the same roundings the per-texel formula makes; the colour step of 8-bit
+// colours is exact), so a texel reads its segment with two 16-byte loads.
 struct RampSmem {
     float value[16];
-    float rgb[16][3];
+    float4 seg[15][2];  // {v0, dv, c0.r, c0.g}, {c0.b, dc.r, dc.g, dc.b}
 };
 
 // One texel: colour of value x, opacity from its count, over base texel b
 // (packed RGBA, little-endian bytes) when there is a base.  The segment is
 // the number of interior stops at or below x (stops strictly increase), a
 // loop of uniform trip count over the broadcast stop values.
-__device__ __forceinline__ uint32_t compose_one(const RampSmem& r, int n_stops, float alpha, uint32_t count_min,
-                                                float x, uint32_t count, bool has_base, uint32_t b)
+__device__ __forceinline__ uint32_t compose_one(const RampSmem& r, int n_stops, float v_first, float v_last,
+                                                float alpha, uint32_t count_min, float x, uint32_t count,
+                                                bool has_base, uint32_t b)
 {
-    const int last = n_stops - 1;
-    if (!(x > r.value[0])) x = r.value[0];
-    if (x > r.value[last]) x = r.value[last];
+    if (!(x > v_first)) x = v_first;
+    if (x > v_last) x = v_last;
     int k = 0;
-    for (int j = 1; j < last; ++j) k += x >= r.value[j] ? 1 : 0;
-    const float t = __fdiv_rn(__fsub_rn(x, r.value[k]), __fsub_rn(r.value[k + 1], r.value[k]));
+    for (int j = 1; j < n_stops - 1; ++j) k += x >= r.value[j] ? 1 : 0;
+    const float4 s0 = r.seg[k][0], s1 = r.seg[k][1];
+    const float t = __fdiv_rn(__fsub_rn(x, s0.x), s0.y);
     const float a = count >= count_min ? alpha : 0.0f;
+    const float col[3] = {__fadd_rn(s0.z, __fmul_rn(t, s1.y)), __fadd_rn(s0.w, __fmul_rn(t, s1.z)),
+                          __fadd_rn(s1.x, __fmul_rn(t, s1.w))};
+    const float na = __fsub_rn(1.0f, a);
     uint32_t o = 0u;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const float c0 = r.rgb[k][c], c1 = r.rgb[k + 1][c];
-        const float col = __fadd_rn(c0, __fmul_rn(t, __fsub_rn(c1, c0)));
         const float bc = (float)((b >> (8 * c)) & 0xffu);
-        const uint8_t ch = has_base ? to_u8(__fadd_rn(__fmul_rn(a, col), __fmul_rn(__fsub_rn(1.0f, a), bc)))
-                                    : to_u8(col);
-        o |= (uint32_t)ch << (8 * c);
+        const uint32_t ch = has_base ? to_u8(__fadd_rn(__fmul_rn(a, col[c]), __fmul_rn(na, bc))) : to_u8(col[c]);
+        o |= ch << (8 * c);
     }
-    const uint32_t oa = has_base ? (b >> 24) : (uint32_t)to_u8(__fmul_rn(255.0f, a));
+    const uint32_t oa = has_base ? (b >> 24) : to_u8(__fmul_rn(255.0f, a));
     return o | (oa << 24);
 }
 
@@ -61,12 +61,17 @@ __global__ void k_compose(const float* __restrict__ value, const uint32_t* __res
     __shared__ RampSmem ramp;
     for (int i = threadIdx.x; i < 16; i += blockDim.x) {
         ramp.value[i] = cm.value[i];
-        ramp.rgb[i][0] = (float)cm.rgb[i][0];
-        ramp.rgb[i][1] = (float)cm.rgb[i][1];
-        ramp.rgb[i][2] = (float)cm.rgb[i][2];
+        if (i + 1 < cm.n_stops) {
+            const float c0r = (float)cm.rgb[i][0], c0g = (float)cm.rgb[i][1], c0b = (float)cm.rgb[i][2];
+            ramp.seg[i][0] = make_float4(cm.value[i], __fsub_rn(cm.value[i + 1], cm.value[i]), c0r, c0g);
+            ramp.seg[i][1] = make_float4(c0b, __fsub_rn((float)cm.rgb[i + 1][0], c0r),
+                                         __fsub_rn((float)cm.rgb[i + 1][1], c0g),
+                                         __fsub_rn((float)cm.rgb[i + 1][2], c0b));
+        }
     }
     __syncthreads();
     const int ns = cm.n_stops;
+    const float v_first = cm.value[0], v_last = cm.value[ns - 1];
     const float alpha = cm.alpha;
     const uint32_t cmin = cm.count_min;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -79,13 +84,15 @@ __global__ void k_compose(const float* __restrict__ value, const uint32_t* __res
         const float4 v = __ldg(reinterpret_cast<const float4*>(value) + q);
         const uint4 c = __ldg(reinterpret_cast<const uint4*>(count) + q);
         const uint4 b = has_base ? __ldg(reinterpret_cast<const uint4*>(base32) + q) : make_uint4(0u, 0u, 0u, 0u);
-        reinterpret_cast<uint4*>(out32)[q] = make_uint4(compose_one(ramp, ns, alpha, cmin, v.x, c.x, has_base, b.x),
-                                                        compose_one(ramp, ns, alpha, cmin, v.y, c.y, has_base, b.y),
-                                                        compose_one(ramp, ns, alpha, cmin, v.z, c.z, has_base, b.z),
-                                                        compose_one(ramp, ns, alpha, cmin, v.w, c.w, has_base, b.w));
+        reinterpret_cast<uint4*>(out32)[q] =
+            make_uint4(compose_one(ramp, ns, v_first, v_last, alpha, cmin, v.x, c.x, has_base, b.x),
+                       compose_one(ramp, ns, v_first, v_last, alpha, cmin, v.y, c.y, has_base, b.y),
+                       compose_one(ramp, ns, v_first, v_last, alpha, cmin, v.z, c.z, has_base, b.z),
+                       compose_one(ramp, ns, v_first, v_last, alpha, cmin, v.w, c.w, has_base, b.w));
     }
     for (int64_t i = 4 * n4 + tid; i < n; i += stride)
-        out32[i] = compose_one(ramp, ns, alpha, cmin, value[i], count[i], has_base, has_base ? base32[i] : 0u);
+        out32[i] = compose_one(ramp, ns, v_first, v_last, alpha, cmin, value[i], count[i], has_base,
+                               has_base ? base32[i] : 0u);
 }
 
 __device__ __forceinline__ float smooth_step(float e0, float e1, float x)
@@ -96,7 +103,7 @@ __device__ __forceinline__ float smooth_step(float e0, float e1, float x)
     return __fmul_rn(__fmul_rn(t, t), __fsub_rn(3.0f, __fmul_rn(2.0f, t)));
 }
 
-__device__ __forceinline__ uint32_t snow_rgba(float a) { return 0x00ffffffu | ((uint32_t)to_u8(__fmul_rn(255.0f, a)) << 24); }
+__device__ __forceinline__ uint32_t snow_rgba(float a) { return 0x00ffffffu | (to_u8(__fmul_rn(255.0f, a)) << 24); }
 
 // Four texels per thread when every buffer is 16-byte aligned, then a scalar tail.
 __global__ void k_snow(const float* __restrict__ h, const float* __restrict__ nz, int64_t n, float a0, float a1,
