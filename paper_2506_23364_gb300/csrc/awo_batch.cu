@@ -281,7 +281,8 @@ __global__ void __launch_bounds__(THREADS) k_batch_simulate(const __grid_constan
                 AWO_LANE_START(ok, st, jj, q.W);
             const bool cap0 = ok && q.max_steps == 0u;
             my_cap += cap0 ? 1u : 0u;
-            my_traj += cap0 ? 1u : 0u;
+            my_traj += ok ? 1u : 0u;  // particles are counted when they start
+            AWO_FOLD_MOVES();
             live = live || (ok && !cap0);
             advance(cur_ci, cur_j, take, q.N);
             cur_t += take;

@@ -178,7 +178,8 @@ __global__ void __launch_bounds__(SIM_THREADS) k_simulate(const __grid_constant_
                     AWO_LANE_START(ok, st, jj, a.W);
                 const bool cap0 = ok && a.max_steps == 0u;  // capped at the release visit
                 my_cap += cap0 ? 1u : 0u;
-                my_traj += cap0 ? 1u : 0u;
+                my_traj += ok ? 1u : 0u;  // particles are counted when they start
+                AWO_FOLD_MOVES();
                 live = live || (ok && !cap0);
                 advance(cur_ci, cur_j, take, a.N);
                 cur_t += take;
