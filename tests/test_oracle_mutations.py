@@ -1,6 +1,8 @@
 """The oracle's pins catch plausible mistakes: each mutation below plants one
 in a copy of ``oracle/awo_oracle.c`` (a dropped term, a flipped sign, a
-transposed operand, a wrong index or tie rule), and the oracle's own pin
+transposed operand, a wrong index or tie rule -- in the particle path, the
+terrain stages, the mipmap, compose, snow cover and the soft-deposit
+forward and gradient), and the oracle's own pin
 tests, run against the mutated copy in a sandbox, must fail.  The unmutated
 copy must pass.  Nothing here touches the repository's oracle build."""
 import os
@@ -15,7 +17,7 @@ SRC = os.path.join(ROOT, "oracle", "awo_oracle.c")
 
 PIN_FILES = ["test_oracle_closed_forms.py", "test_oracle_bruteforce.py", "test_oracle_invariants.py",
              "test_oracle_philox.py", "test_oracle_normals_release.py", "test_oracle_lod.py",
-             "test_oracle_release_texture.py"]
+             "test_oracle_release_texture.py", "test_oracle_compose_snow.py", "test_oracle_soft.py"]
 
 # (name, exact text in awo_oracle.c, replacement)
 MUTATIONS = [
@@ -43,6 +45,16 @@ MUTATIONS = [
      "int sel = (t_lo < tan2[i]) && (tan2[i] <= t_hi);"),
     ("texel centre offset", "double c = ldexp((double)a + 0.5, -r) - 0.5;", "double c = ldexp((double)a, -r) - 0.5;"),
     ("mipmap count wraps", "sum > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)sum", "(uint32_t)sum"),
+    ("colour ramp step reversed", "const real c = c0 + t * (c1 - c0);", "const real c = c1 + t * (c0 - c1);"),
+    ("blend weights swapped", "to_u8(a * c + ((real)1 - a) * (real)base[4 * i + ch])",
+     "to_u8(((real)1 - a) * c + a * (real)base[4 * i + ch])"),
+    ("smoothstep polynomial", "return t * t * ((real)3 - (real)2 * t);", "return t * ((real)3 - (real)2 * t);"),
+    ("snow slope edges swapped", "const real c0 = (real)cos(s_lo * r), c1 = (real)cos(s_hi * r);",
+     "const real c0 = (real)cos(s_hi * r), c1 = (real)cos(s_lo * r);"),
+    ("soft remainder dropped", "deposit[sp.cell[sp.n]] += w * sp.S[sp.n];", ";"),
+    ("soft survival sign", "double S1 = S / (1.0 + exp(-e1 / tau));", "double S1 = S / (1.0 + exp(e1 / tau));"),
+    ("adjoint drag factor dropped", "double lam = abar[m] * sp.S[m - 1] * dsig + (1.0 - kD) * lam_next;",
+     "double lam = abar[m] * sp.S[m - 1] * dsig + lam_next;"),
 ]
 
 
