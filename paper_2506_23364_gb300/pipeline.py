@@ -143,6 +143,26 @@ class Overlay:
         self.simulate(params, True, stream)
         self.overlay(params.gravity, stream)
 
+    def capture(self, slope_lo_deg: float, slope_hi_deg: float, params: SimParams,
+                decode_scale: float = 0.1) -> torch.cuda.CUDAGraph:
+        """Records the whole workflow (from the DEM already on the device) in a
+        CUDA graph; ``replay()`` relaunches it after the DEM buffer is refilled,
+        with no per-kernel host work.  The library makes no host
+        synchronisation and no allocation inside the calls, and the release
+        count stays on the device, so the graph is the same for every DEM."""
+        self.run(slope_lo_deg, slope_hi_deg, params, decode_scale)  # warm per-device caches outside the capture
+        torch.cuda.synchronize(self.device)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self.run(slope_lo_deg, slope_hi_deg, params, decode_scale)
+        self.graph = graph
+        return graph
+
+    def replay(self):
+        if getattr(self, "graph", None) is None:
+            raise RuntimeError("capture() first")
+        self.graph.replay()
+
     # ------------------------------------------------------------------
     def n_release(self) -> int:
         return int(self.n_rel.item())

@@ -85,3 +85,27 @@ def test_snow_cover_bitexact():
     assert np.array_equal(a.cpu().numpy(), ra)
     assert np.array_equal(rgba.cpu().numpy(), rrgba)
     assert 0.0 < ra.mean() < 1.0
+
+
+def test_overlay_graph_replay_bitexact():
+    """The whole single-region workflow captured in a CUDA graph and replayed
+    on a second DEM gives the oracle's overlay for that DEM."""
+    w = inputs.mid()
+    dem2 = inputs.fbm(512, 0.8, seed=77, relief=1500.0)
+    q2 = inputs.quantise_dm(dem2)
+    cw = inputs.crop(w, 512)
+    ov = awo.Overlay(512, 512, cw.cell_size, quantised=True, levels=3)
+    ov.load_dem(cw.dem_u16)
+    p = awo.SimParams.make(traj_per_cell=8, max_steps=500, seed=3)
+    ov.capture(30.0, 45.0, p)
+    ov.load_dem(q2)
+    ov.replay()
+    torch.cuda.synchronize()
+    got = ov.host_results()
+    h = oracle.decode_u16(q2)
+    ref = oracle.overlay(h, cw.cell_size, 30.0, 45.0, oracle.SimParams(traj_per_cell=8, max_steps=500, seed=3), 3)
+    assert np.array_equal(got["cells"], ref["cells"])
+    assert np.array_equal(got["count"], ref["count"]) and np.array_equal(got["vel"], ref["vel"])
+    for l in range(3):
+        assert np.array_equal(got["count_lv"][l], ref["count_lv"][l])
+        assert np.array_equal(got["vel_lv"][l], ref["vel_lv"][l])
