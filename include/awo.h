@@ -12,8 +12,9 @@
  *
  * Conventions shared by every call:
  *  - Pointers named d_* are DEVICE pointers on the current CUDA device; the
- *    caller allocates and owns every buffer.  The library keeps no device
- *    memory of its own and never allocates.
+ *    caller allocates and owns every buffer.  The library never allocates;
+ *    the only device memory of its own is the fixed 128 KiB scratch array of
+ *    awo_release_noalloc (a static device array in the library image).
  *  - Rasters are row-major, width x height, index y * width + x; cell (x, y)
  *    has its centre at cell coordinates (u, v) = (x, y).
  *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
