@@ -783,7 +783,7 @@ def run_reference(args, R: Ranks):
                          max_steps=w.max_steps, seed=w.seed)
     threads = args.cpu_threads or os.cpu_count() or 1
     total = args.steps + max(args.warmup, 0)
-    per_step_s = max(1.0, min(10.0, 150.0 / max(total, 1)))
+    per_step_s = max(min(1.0, args.cpu_seconds), min(10.0, args.cpu_seconds, 150.0 / max(total, 1)))
     rng = np.random.default_rng(777)
     rate = _oracle_rate(oracle, h, w.cell_size, cells, p, threads, rng)
     k = int(min(cells.size, max(threads, rate * per_step_s)))
