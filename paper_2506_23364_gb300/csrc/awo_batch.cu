@@ -9,12 +9,14 @@
 //   k_batch_starts   per release cell of every request: its start record and
 //                    the release visits of its particles;
 //   k_batch_simulate persistent: warps take chunks of consecutive particles
-//                    from one global counter over all requests.  A warp runs one request at
-//                    a time; it switches only when all its lanes are idle,
-//                    which happens at request boundaries only, so the
-//                    request's constants are warp-uniform.  Lanes refill as
-//                    in the single-request kernel (AWO_REFILL_LANE) or start
-//                    32 particles together (AWO_REFILL_WARP).
+//                    from one global counter over all requests.  A warp
+//                    runs one request at a time; it switches only when all
+//                    its lanes are idle, which happens at request
+//                    boundaries only, so the request's constants are
+//                    warp-uniform.  Lanes refill as in the single-request
+//                    kernel (AWO_REFILL_LANE) or start 32 particles together
+//                    (AWO_REFILL_WARP); each iteration makes two moves from
+//                    one Philox block, as there.
 // The per-move arithmetic is the one of awo_particle.cuh, so every request's
 // rasters equal those of awo_simulate on that request alone.
 #include <math.h>

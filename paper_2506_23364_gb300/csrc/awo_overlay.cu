@@ -1,8 +1,9 @@
 // awo_overlay.cu -- velocity indicator and overlay mipmap (Sec. 3, Fig. 4).
 //
 // Both are streaming passes.  The mipmap is built level by level: each thread
-// reduces one 2x2 block of the level above (counts summed in 64 bits and
-// saturated, velocities by max), so every level reads its parent once.
+// reduces 2x2 blocks of the level above (two output texels from 16-byte rows
+// when the level allows it; counts summed in 64 bits and saturated,
+// velocities by max), so every level reads its parent once.
 #include "awo_internal.cuh"
 
 namespace awo {

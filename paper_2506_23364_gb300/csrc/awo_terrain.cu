@@ -1,8 +1,10 @@
 // awo_terrain.cu -- DEM decode, normals/steepness and release-cell selection.
 //
 // These are streaming passes over the W x H grid (HBM-bound).  Each kernel is
-// a grid-stride loop sized in multiples of the SM count.  Arithmetic uses
-// explicit round-to-nearest intrinsics so no multiply-add is ever fused.
+// a grid-stride loop sized in multiples of the SM count, moving 16-byte
+// vectors when its buffers are aligned (a general path covers ragged sizes
+// and offsets).  Arithmetic uses explicit round-to-nearest intrinsics so no
+// multiply-add is ever fused.
 #include <math.h>
 #include <stdio.h>
 
