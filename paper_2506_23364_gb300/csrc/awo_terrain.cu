@@ -324,6 +324,57 @@ __device__ __forceinline__ float texel_centre(uint32_t a, float scale, float n_m
     return fminf(fmaxf(c, 0.0f), n_m1);
 }
 
+// A run of RT_CELLS texels of a texture at 2^R times the DEM resolution
+// (R >= 0) whose first texel index a along the row is a multiple of 2^R (every
+// run of the kernel below: runs start at multiples of RT_CELLS and rows have
+// W 2^R texels).  Texel a + k is centred at u = A + (2k + 1 - 2^R) / 2^(R+1)
+// with A = a / 2^R, so its footprint column is A + delta(k) and its weight
+// frac(k), both fixed for the run -- exactly what texel_centre and the floor
+// give when no clamping occurs.
+template <int R>
+struct TexRun {
+    static constexpr int S = 1 << R;
+    __host__ __device__ static constexpr int num(int k) { return 2 * k + 1 - S; }
+    __host__ __device__ static constexpr int fdiv(int x, int d) { return x >= 0 ? x / d : -((-x + d - 1) / d); }
+    __host__ __device__ static constexpr int delta(int k) { return fdiv(num(k), 2 * S); }
+    __host__ __device__ static constexpr float frac(int k) { return (float)(num(k) - delta(k) * 2 * S) / (float)(2 * S); }
+    __host__ __device__ static constexpr float one_minus_frac(int k) { return 1.0f - frac(k); }  // exact: frac has <= 4 bits
+    static constexpr int DMIN = delta(0), DMAX = delta(RT_CELLS - 1);
+    static constexpr int NC = DMAX - DMIN + 2;  // footprint columns the run reads
+};
+
+// Selection bits of a run in one texture row, away from both row ends: the
+// two tan^2 rows under it are loaded once (NC values each) and every texel
+// interpolates with compile-time weights.  Same arithmetic as the general
+// path, texel by texel.
+template <int R>
+__device__ __forceinline__ uint32_t texel_run_bits(const float* __restrict__ tan2, int row, int dj, int A, float oy,
+                                                   float fy, float t_lo, float t_hi)
+{
+    using T = TexRun<R>;
+    float top[T::NC], bot[T::NC];
+    const float* p = tan2 + row + A + T::DMIN;
+#pragma unroll
+    for (int i = 0; i < T::NC; ++i) {
+        top[i] = __ldg(p + i);
+        bot[i] = __ldg(p + dj + i);
+    }
+    uint32_t bits = 0u;
+#pragma unroll
+    for (int k = 0; k < RT_CELLS; ++k) {
+        const int c = T::delta(k) - T::DMIN;
+        const float fx = T::frac(k), ox = T::one_minus_frac(k);
+        const float tp = __fadd_rn(__fmul_rn(top[c], ox), __fmul_rn(top[c + 1], fx));
+        const float bt = __fadd_rn(__fmul_rn(bot[c], ox), __fmul_rn(bot[c + 1], fx));
+        const float Tk = __fadd_rn(__fmul_rn(tp, oy), __fmul_rn(bt, fy));
+        bits |= ((t_lo <= Tk && Tk <= t_hi) ? 1u : 0u) << k;
+    }
+    return bits;
+}
+
+// R >= 0: runs in one row away from the row ends take texel_run_bits; the
+// rest (and every run when R < 0, written R = -1) the general per-texel path.
+template <int R>
 __global__ void __launch_bounds__(RT_THREADS) k_release_texture_mask(const float* __restrict__ tan2, int W, int H,
                                                                      uint32_t Wr, int64_t n, float scale,
                                                                      float t_lo, float t_hi,
@@ -345,39 +396,49 @@ __global__ void __launch_bounds__(RT_THREADS) k_release_texture_mask(const float
     float fy = __fsub_rn(v, __int2float_rn(j0)), oy = __fsub_rn(1.0f, fy);
     int row = j0 * W, dj = j0 + 1 < H ? W : 0;
     uint32_t bits = 0u;
-    // footprint of the previous texel: on a finer texture 2^r consecutive
-    // texels share one, so its four values are loaded once
-    int o_prev = -1;
-    float t00 = 0.0f, t10 = 0.0f, t01 = 0.0f, t11 = 0.0f;
+    bool done = false;
+    if (R >= 0 && base + RT_CELLS <= n32 && a + RT_CELLS <= Wr) {
+        const int A = (int)(a >> (R >= 0 ? R : 0));
+        if (A + TexRun<(R >= 0 ? R : 0)>::DMIN >= 0 && A + TexRun<(R >= 0 ? R : 0)>::DMAX + 1 <= W - 2) {
+            bits = texel_run_bits<(R >= 0 ? R : 0)>(tan2, row, dj, A, oy, fy, t_lo, t_hi);
+            done = true;
+        }
+    }
+    if (!done) {
+        // footprint of the previous texel: on a finer texture 2^r consecutive
+        // texels share one, so its four values are loaded once
+        int o_prev = -1;
+        float t00 = 0.0f, t10 = 0.0f, t01 = 0.0f, t11 = 0.0f;
 #pragma unroll
-    for (int k = 0; k < RT_CELLS; ++k) {
-        if (base + k < n32) {
-            const float u = texel_centre(a, scale, wm1);
-            const int i0 = __float2int_rd(u);
-            const float fx = __fsub_rn(u, __int2float_rn(i0));
-            const int o = row + i0;
-            if (o != o_prev) {
-                const int di = i0 + 1 < W ? 1 : 0;
-                t00 = __ldg(tan2 + o);
-                t10 = __ldg(tan2 + o + di);
-                t01 = __ldg(tan2 + o + dj);
-                t11 = __ldg(tan2 + o + dj + di);
-                o_prev = o;
-            }
-            const float ox = __fsub_rn(1.0f, fx);
-            const float top = __fadd_rn(__fmul_rn(t00, ox), __fmul_rn(t10, fx));
-            const float bot = __fadd_rn(__fmul_rn(t01, ox), __fmul_rn(t11, fx));
-            const float T = __fadd_rn(__fmul_rn(top, oy), __fmul_rn(bot, fy));
-            bits |= ((t_lo <= T && T <= t_hi) ? 1u : 0u) << k;
-            if (++a == Wr) {
-                a = 0u;
-                ++b;
-                v = texel_centre(b, scale, hm1);
-                j0 = __float2int_rd(v);
-                fy = __fsub_rn(v, __int2float_rn(j0));
-                oy = __fsub_rn(1.0f, fy);
-                row = j0 * W;
-                dj = j0 + 1 < H ? W : 0;
+        for (int k = 0; k < RT_CELLS; ++k) {
+            if (base + k < n32) {
+                const float u = texel_centre(a, scale, wm1);
+                const int i0 = __float2int_rd(u);
+                const float fx = __fsub_rn(u, __int2float_rn(i0));
+                const int o = row + i0;
+                if (o != o_prev) {
+                    const int di = i0 + 1 < W ? 1 : 0;
+                    t00 = __ldg(tan2 + o);
+                    t10 = __ldg(tan2 + o + di);
+                    t01 = __ldg(tan2 + o + dj);
+                    t11 = __ldg(tan2 + o + dj + di);
+                    o_prev = o;
+                }
+                const float ox = __fsub_rn(1.0f, fx);
+                const float top = __fadd_rn(__fmul_rn(t00, ox), __fmul_rn(t10, fx));
+                const float bot = __fadd_rn(__fmul_rn(t01, ox), __fmul_rn(t11, fx));
+                const float T = __fadd_rn(__fmul_rn(top, oy), __fmul_rn(bot, fy));
+                bits |= ((t_lo <= T && T <= t_hi) ? 1u : 0u) << k;
+                if (++a == Wr) {
+                    a = 0u;
+                    ++b;
+                    v = texel_centre(b, scale, hm1);
+                    j0 = __float2int_rd(v);
+                    fy = __fsub_rn(v, __int2float_rn(j0));
+                    oy = __fsub_rn(1.0f, fy);
+                    row = j0 * W;
+                    dj = j0 + 1 < H ? W : 0;
+                }
             }
         }
     }
@@ -580,7 +641,12 @@ extern "C" awo_status awo_release_texture(const float* d_tan2, awo_grid g, int32
     const float t_lo = tan2_of_degrees(slope_lo_deg), t_hi = tan2_of_degrees(slope_hi_deg);
     const float scale = ldexpf(1.0f, -release_log2);
     cudaStream_t s = as_stream(stream);
-    k_release_texture_mask<<<tiles, RT_THREADS, 0, s>>>(d_tan2, g.width, g.height, (uint32_t)wr, n, scale, t_lo,
+    auto kern = release_log2 == 0   ? k_release_texture_mask<0>
+                : release_log2 == 1 ? k_release_texture_mask<1>
+                : release_log2 == 2 ? k_release_texture_mask<2>
+                : release_log2 == 3 ? k_release_texture_mask<3>
+                                    : k_release_texture_mask<-1>;
+    kern<<<tiles, RT_THREADS, 0, s>>>(d_tan2, g.width, g.height, (uint32_t)wr, n, scale, t_lo,
                                                         t_hi, d_mask, tile_count);
     k_release_scan<<<1, 1024, 0, s>>>(tile_count, tiles, tile_offset, d_n);
     k_mask_scatter<<<tiles, RT_THREADS, 0, s>>>(d_mask, n, tile_offset, d_texels);
