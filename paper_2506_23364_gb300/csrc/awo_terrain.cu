@@ -346,18 +346,32 @@ struct TexRun {
 // Selection bits of a run in one texture row, away from both row ends: the
 // two tan^2 rows under it are loaded once (NC values each) and every texel
 // interpolates with compile-time weights.  Same arithmetic as the general
-// path, texel by texel.
-template <int R>
+// path, texel by texel.  VEC: tan2 + row + A is 16-byte aligned (tan2
+// aligned, W and A multiples of 4), so the aligned groups of four among the
+// NC columns are read as float4 -- a quarter of the load instructions, which
+// bound this pass through the L1 otherwise.
+template <int R, bool VEC>
 __device__ __forceinline__ uint32_t texel_run_bits(const float* __restrict__ tan2, int row, int dj, int A, float oy,
                                                    float fy, float t_lo, float t_hi)
 {
     using T = TexRun<R>;
     float top[T::NC], bot[T::NC];
-    const float* p = tan2 + row + A + T::DMIN;
+    const float* p = tan2 + row + A;
 #pragma unroll
-    for (int i = 0; i < T::NC; ++i) {
-        top[i] = __ldg(p + i);
-        bot[i] = __ldg(p + dj + i);
+    for (int i = T::DMIN; i <= T::DMAX + 1; ++i) {
+        const int g = i & ~3;  // start of i's aligned group of four (relative to A)
+        const bool whole = VEC && g >= T::DMIN && g + 3 <= T::DMAX + 1;
+        if (whole && i == g) {
+            const float4 qt = __ldg(reinterpret_cast<const float4*>(p + i));
+            const float4 qb = __ldg(reinterpret_cast<const float4*>(p + dj + i));
+            top[i - T::DMIN] = qt.x, top[i - T::DMIN + 1] = qt.y, top[i - T::DMIN + 2] = qt.z,
+                          top[i - T::DMIN + 3] = qt.w;
+            bot[i - T::DMIN] = qb.x, bot[i - T::DMIN + 1] = qb.y, bot[i - T::DMIN + 2] = qb.z,
+                          bot[i - T::DMIN + 3] = qb.w;
+        } else if (!whole) {
+            top[i - T::DMIN] = __ldg(p + i);
+            bot[i - T::DMIN] = __ldg(p + dj + i);
+        }
     }
     uint32_t bits = 0u;
 #pragma unroll
@@ -374,7 +388,8 @@ __device__ __forceinline__ uint32_t texel_run_bits(const float* __restrict__ tan
 
 // R >= 0: runs in one row away from the row ends take texel_run_bits; the
 // rest (and every run when R < 0, written R = -1) the general per-texel path.
-template <int R>
+// VEC as in texel_run_bits (host-checked alignment of tan2 and W; R <= 2).
+template <int R, bool VEC>
 __global__ void __launch_bounds__(RT_THREADS) k_release_texture_mask(const float* __restrict__ tan2, int W, int H,
                                                                      uint32_t Wr, int64_t n, float scale,
                                                                      float t_lo, float t_hi,
@@ -400,7 +415,7 @@ __global__ void __launch_bounds__(RT_THREADS) k_release_texture_mask(const float
     if (R >= 0 && base + RT_CELLS <= n32 && a + RT_CELLS <= Wr) {
         const int A = (int)(a >> (R >= 0 ? R : 0));
         if (A + TexRun<(R >= 0 ? R : 0)>::DMIN >= 0 && A + TexRun<(R >= 0 ? R : 0)>::DMAX + 1 <= W - 2) {
-            bits = texel_run_bits<(R >= 0 ? R : 0)>(tan2, row, dj, A, oy, fy, t_lo, t_hi);
+            bits = texel_run_bits<(R >= 0 ? R : 0), VEC>(tan2, row, dj, A, oy, fy, t_lo, t_hi);
             done = true;
         }
     }
@@ -641,11 +656,14 @@ extern "C" awo_status awo_release_texture(const float* d_tan2, awo_grid g, int32
     const float t_lo = tan2_of_degrees(slope_lo_deg), t_hi = tan2_of_degrees(slope_hi_deg);
     const float scale = ldexpf(1.0f, -release_log2);
     cudaStream_t s = as_stream(stream);
-    auto kern = release_log2 == 0   ? k_release_texture_mask<0>
-                : release_log2 == 1 ? k_release_texture_mask<1>
-                : release_log2 == 2 ? k_release_texture_mask<2>
-                : release_log2 == 3 ? k_release_texture_mask<3>
-                                    : k_release_texture_mask<-1>;
+    // float4 reads of tan2 rows: base 16-byte aligned and W a multiple of 4,
+    // so that every row and every run start (a multiple of 16 / 2^r cells) is
+    const bool vec = (((uintptr_t)d_tan2) & 15u) == 0 && (g.width & 3) == 0;
+    auto kern = release_log2 == 0   ? (vec ? k_release_texture_mask<0, true> : k_release_texture_mask<0, false>)
+                : release_log2 == 1 ? (vec ? k_release_texture_mask<1, true> : k_release_texture_mask<1, false>)
+                : release_log2 == 2 ? (vec ? k_release_texture_mask<2, true> : k_release_texture_mask<2, false>)
+                : release_log2 == 3 ? k_release_texture_mask<3, false>
+                                    : k_release_texture_mask<-1, false>;
     kern<<<tiles, RT_THREADS, 0, s>>>(d_tan2, g.width, g.height, (uint32_t)wr, n, scale, t_lo,
                                                         t_hi, d_mask, tile_count);
     k_release_scan<<<1, 1024, 0, s>>>(tile_count, tiles, tile_offset, d_n);

@@ -54,6 +54,26 @@ def test_release_texture_bitexact(r, shape):
     assert np.array_equal(tex_got, tex_ref)
 
 
+@pytest.mark.parametrize("r", [0, 1, 2, 3])
+@pytest.mark.parametrize("W,offset", [(256, 0), (256, 1), (258, 0), (253, 0)])
+def test_release_texture_load_paths(r, W, offset):
+    """Runs of texels away from the row ends read the two tan^2 rows once,
+    as float4 when tan2 is 16-byte aligned and W a multiple of 4 (r <= 2),
+    else as scalars; the row ends take the per-texel path.  Every layout
+    gives the oracle's texture."""
+    H = 37
+    h = inputs.fbm(W, 0.8, seed=W + r, relief=1800.0)[:H, :W].astype(np.float32)
+    g, t2 = _tan2(h, 10.0)
+    t2h = t2.cpu().numpy()
+    buf = torch.empty(H * W + offset, dtype=torch.float32, device="cuda")
+    buf[offset:] = t2.reshape(-1)
+    m_ref, tex_ref = oracle.release_texture(t2h, r, 29.0, 46.0)
+    m_got, tex_got = _gpu_release_texture(buf[offset:].view(H, W), g, r, 29.0, 46.0)
+    assert tex_ref.size > 100
+    assert np.array_equal(m_got, m_ref)
+    assert np.array_equal(tex_got, tex_ref)
+
+
 def test_release_texture_unaligned_mask_and_r0():
     h = inputs.fbm(200, 0.8, seed=3, relief=1500.0).astype(np.float32)
     g, t2 = _tan2(h, 10.0)
