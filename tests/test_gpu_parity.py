@@ -7,6 +7,7 @@ has a tolerance.  Inputs are the seeded synthetic workloads (tiny, mid, the
 large DEM's 1024^2 crop, and the full 8192^2 DEM with sampled release cells).
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -222,8 +223,10 @@ def test_large_crop_workflow_bitexact(large_dem):
 
 def test_large_full_size_sampled(large_dem):
     """8192^2 in the benchmark's launch configuration: terrain stages bit-exact
-    over the whole grid; the full particle run checked by its invariants; and
-    a sample of 3000 release cells run alone, bit-exact against the oracle."""
+    over the whole grid; the full particle run (3.36 M release cells x 256
+    particles) checked by its invariants and then cell by cell against the
+    oracle's rasters and statistics (the oracle on every host core, about 15 s
+    on 16); and a sample of 3000 release cells run alone, bit-exact."""
     n = 8192
     lo, hi = inputs.LARGE_RELEASE_DEG
     op = _oparams(traj_per_cell=256, max_steps=8000)
@@ -251,6 +254,15 @@ def test_large_full_size_sampled(large_dem):
     for l in range(1, 6):
         assert np.array_equal(ov.count_lv[l - 1].cpu().numpy().view(np.uint32), cl[l])
         assert np.array_equal(ov.vel_lv[l - 1].cpu().numpy(), vl[l])
+    # every cell of the full run against the oracle
+    threads = min(16, os.cpu_count() or 1)
+    c64_all, maxe_all, st_all = oracle.simulate_threaded(h, inputs.CELL_SIZE_M, rel, op, threads=threads)
+    assert np.array_equal(cnt, oracle.counts_u32(c64_all))
+    del c64_all
+    assert np.array_equal(maxe, maxe_all)
+    del maxe_all
+    for k in ("total_steps", "n_traj", "n_exited", "n_capped", "n_stopped"):
+        assert st[k] == st_all[k], k
     # sampled release cells, same kernel and launch shape
     rng = np.random.default_rng(0)
     sub = np.sort(rng.choice(rel, 3000, replace=False)).astype(np.uint32)
