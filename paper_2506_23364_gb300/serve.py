@@ -10,14 +10,18 @@ changes).  A server re-runs it for many users at once:
   the device-memory budget has room for their buffers -- requests that arrive
   while others run are admitted into the next micro-batch, they do not wait
   for the running ones to finish;
+* a submitted DEM is copied into page-locked host memory on the submitting
+  thread (within a host staging budget), so the scheduler thread only issues
+  asynchronous copies when the request is admitted;
 * an admitted micro-batch (up to ``max_batch`` requests) runs on its own CUDA
   stream: host-to-device copy of the DEMs, terrain stages, ONE batched
   particle launch for all of them (``awo_simulate_batched``), velocity and
   mipmap, device-to-host copy of the overlays -- so micro-batches on
   different slots overlap on the GPU;
 * completion is seen through a CUDA event; the request's future then holds
-  the overlay (count and velocity rasters of every mipmap level), its
-  statistics and its latency.
+  the overlay (count and velocity rasters of every mipmap level, as arrays
+  over the page-locked buffers the device wrote them to: no further copy),
+  its statistics and its latency.
 
 A request whose buffers exceed the whole budget is rejected; a request with
 invalid parameters fails alone; queued requests can be cancelled.  Because
@@ -53,6 +57,8 @@ class OverlayRequest:
     decode_scale: float = 0.1
     id: int = -1
     t_submit: float = 0.0
+    staged: object = field(default=None, repr=False)  # page-locked copy of the DEM, set by the executor
+    staged_bytes: int = 0
 
     @property
     def quantised(self) -> bool:
@@ -183,6 +189,17 @@ class GpuExecutor:
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(n_slots)]
         self.free = list(range(n_slots))
 
+    def stage(self, req: OverlayRequest):
+        """Page-locked host copy of the request's DEM (the source of its
+        asynchronous host-to-device copy)."""
+        torch = self.torch
+        src = np.ascontiguousarray(req.dem)
+        if req.quantised:
+            src = src.view(np.int16)
+        pin = torch.empty(src.shape, dtype=torch.int16 if req.quantised else torch.float32, pin_memory=True)
+        pin.numpy()[...] = src
+        return pin
+
     def launch(self, reqs: list[OverlayRequest], t_admit: float) -> _Flight:
         torch = self.torch
         import paper_2506_23364_gb300 as awo
@@ -191,15 +208,9 @@ class GpuExecutor:
         stream = self.streams[slot]
         params = [awo.SimParams.make(**r.params) for r in reqs]
         with torch.cuda.stream(stream):
-            # pinned staging of the DEMs; the async copies read them later
-            pins = []
-            for r in reqs:
-                src = np.ascontiguousarray(r.dem)
-                if r.quantised:
-                    src = src.view(np.int16)
-                pin = torch.empty(src.shape, dtype=torch.int16 if r.quantised else torch.float32, pin_memory=True)
-                pin.numpy()[...] = src
-                pins.append(pin)
+            # page-locked DEMs (staged at submission, else here); the flight
+            # keeps them until its copies have run
+            pins = [r.staged if r.staged is not None else self.stage(r) for r in reqs]
             batch = awo.Batch([r.dem for r in reqs], [r.cell_size for r in reqs], params,
                               [r.release_deg for r in reqs], quantised=[r.quantised for r in reqs],
                               levels=[r.levels for r in reqs], decode_scale=[r.decode_scale for r in reqs],
@@ -234,9 +245,10 @@ class GpuExecutor:
         rows = hs.tolist()
         res = []
         for r, (hc, hv), row in zip(fl.reqs, outs, rows):
+            # the result owns the page-locked buffers its arrays view
             res.append(OverlayResult(
-                id=r.id, status="ok", count_lv=[h.numpy().view(np.uint32).copy() for h in hc],
-                vel_lv=[h.numpy().copy() for h in hv],
+                id=r.id, status="ok", count_lv=[h.numpy().view(np.uint32) for h in hc],
+                vel_lv=[h.numpy() for h in hv],
                 stats={k: int(v) & 0xFFFFFFFFFFFFFFFF for k, v in zip(awo.STATS_FIELDS, row)},
                 batch_size=len(fl.reqs), t_submit=r.t_submit, t_admit=fl.t_admit))
         self.free.append(fl.slot)
@@ -252,10 +264,13 @@ class OverlayServer:
     """Submit requests from any thread; one scheduler thread drives the GPU."""
 
     def __init__(self, budget_bytes: int = 16 << 30, n_slots: int = 4, max_batch: int = 16, device="cuda",
-                 executor=None, poll_s: float = 50e-6):
+                 executor=None, poll_s: float = 50e-6, host_stage_bytes: int = 4 << 30):
         self.sched = Scheduler(budget_bytes, n_slots, max_batch)
         self.exec = executor if executor is not None else GpuExecutor(n_slots, device)
         self.poll_s = poll_s
+        # DEM bytes of queued requests staged in page-locked memory, and its cap
+        self.host_stage_bytes = int(host_stage_bytes)
+        self.staged_bytes = 0
         self.futures: dict[int, Future] = {}
         self.flights: list = []
         self.lock = threading.Condition()
@@ -268,6 +283,7 @@ class OverlayServer:
     # ---- client side ---------------------------------------------------
     def submit(self, req: OverlayRequest) -> Future:
         fut: Future = Future()
+        self._stage(req)
         with self.lock:
             req.id = self.next_id
             self.next_id += 1
@@ -275,8 +291,10 @@ class OverlayServer:
             self.futures[req.id] = fut
             err = self._validate(req)
             if err:
+                self._unstage(req)
                 self._finish(OverlayResult(req.id, "error", err, t_submit=req.t_submit, t_done=time.perf_counter()))
             elif not self.sched.admissible(req):
+                self._unstage(req)
                 self._finish(OverlayResult(req.id, "rejected", f"needs {req.device_bytes()} device bytes, budget is "
                                            f"{self.sched.budget}", t_submit=req.t_submit, t_done=time.perf_counter()))
             else:
@@ -296,6 +314,7 @@ class OverlayServer:
             r = self.sched.cancel(rid)
             if r is None:
                 return False
+            self._unstage(r)
             self._finish(OverlayResult(rid, "cancelled", t_submit=r.t_submit, t_done=time.perf_counter()))
             return True
 
@@ -307,6 +326,31 @@ class OverlayServer:
             self.stop = True
             self.lock.notify()
         self.thread.join()
+
+    def _stage(self, req: OverlayRequest):
+        """Stages the DEM in page-locked memory on the caller's thread, when the
+        executor can and the host staging budget has room; otherwise the
+        executor stages it when the request is admitted."""
+        stage = getattr(self.exec, "stage", None)
+        if stage is None or self._validate(req):
+            return
+        nbytes = int(req.dem.nbytes)
+        with self.lock:
+            if self.staged_bytes + nbytes > self.host_stage_bytes:
+                return
+            self.staged_bytes += nbytes
+        try:
+            req.staged = stage(req)
+            req.staged_bytes = nbytes
+        except Exception:  # staging is an optimisation: fall back to staging at admission
+            with self.lock:
+                self.staged_bytes -= nbytes
+
+    def _unstage(self, req: OverlayRequest):
+        """Drops a queued request's staging (from the budget; its buffer goes
+        with the request or its flight).  Lock held."""
+        self.staged_bytes -= req.staged_bytes
+        req.staged_bytes = 0
 
     # ---- scheduler thread ----------------------------------------------
     @staticmethod
@@ -382,6 +426,9 @@ class OverlayServer:
                         for r in batch:
                             self._finish(OverlayResult(r.id, "error", str(e), t_submit=r.t_submit, t_admit=t_admit))
                         self.sched.release(batch)
+                    for r in batch:  # staging now belongs to the flight (or is dropped)
+                        self._unstage(r)
+                        r.staged = None
                     self.lock.notify_all()
                 if not self.flights and not self.sched.queue:
                     self.lock.notify_all()

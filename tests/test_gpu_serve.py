@@ -66,6 +66,7 @@ def test_same_result_alone_and_in_the_mix(kw):
     srv, res = _serve(reqs, **kw)
     assert all(r.status == "ok" for r in res), [r.error for r in res]
     assert srv.sched.peak_in_use <= kw["budget_bytes"]
+    assert srv.staged_bytes == 0  # every staged DEM went to its flight
     for a, r in zip(alone, res):
         assert len(r.count_lv) == len(a["count_lv"])
         for l in range(len(r.count_lv)):

@@ -150,3 +150,40 @@ def test_device_bytes_counts_release_texture():
     n = 64 * 96
     assert b1 - b0 == 3 * n * 36 + 4 * n          # 3n more entries, and the 4n-byte mask
     assert b0 - bm == n * 36 - (n // 4) * 37      # a quarter of the entries, with their mask
+
+
+class StagingExecutor(FakeExecutor):
+    """Fake executor that also stages DEMs at submission (as the GPU one does)."""
+
+    def __init__(self, **kw):
+        super().__init__(**kw)
+        self.staged_ids = []
+
+    def stage(self, req):
+        self.staged_ids.append(id(req))
+        return object()
+
+    def launch(self, reqs, t_admit):
+        fl = super().launch(reqs, t_admit)
+        fl["staged"] = [r.staged is not None for r in reqs]
+        return fl
+
+
+def test_host_staging_budget():
+    one = _req(64).dem.nbytes
+    ex = StagingExecutor(auto=False)
+    srv = OverlayServer(budget_bytes=1 << 30, n_slots=1, max_batch=1, executor=ex, host_stage_bytes=3 * one)
+    futs = [srv.submit(_req(64)) for _ in range(6)]
+    time.sleep(0.05)
+    with srv.lock:  # one admitted, five queued: at most three of them staged
+        assert 0 < srv.staged_bytes <= 3 * one
+        queued_staged = sum(r.staged is not None for r in srv.sched.queue)
+        assert queued_staged * one == srv.staged_bytes
+    bad = srv.submit(OverlayRequest(np.zeros((8, 8), np.float32), 10.0, (50.0, 40.0), {}))
+    assert bad.result(timeout=5).status == "error"
+    ex.gate.set()
+    res = [f.result(timeout=10) for f in futs]
+    srv.shutdown()
+    assert all(r.status == "ok" for r in res)
+    assert srv.staged_bytes == 0
+    assert len(ex.staged_ids) >= 3
