@@ -14,7 +14,10 @@
  *  - Pointers named d_* are DEVICE pointers on the current CUDA device; the
  *    caller allocates and owns every buffer.  The library never allocates;
  *    the only device memory of its own is the fixed 128 KiB scratch array of
- *    awo_release_noalloc (a static device array in the library image).
+ *    awo_release_noalloc (a static device array in the library image).  The
+ *    one other state it keeps is a table of texture objects (descriptors of
+ *    a caller's DEM buffer: address, width, height; no copy) that
+ *    awo_simulate reads its gathers through; see there.
  *  - Rasters are row-major, width x height, index y * width + x; cell (x, y)
  *    has its centre at cell coordinates (u, v) = (x, y).
  *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
@@ -233,6 +236,15 @@ awo_status awo_release_noalloc(const float* d_tan2, awo_grid g, double slope_lo_
  * Workspace: at least awo_simulate_workspace_bytes(n_cells_max) bytes,
  * 16-byte aligned (a work counter, the statistics, and a start record of up
  * to 32 bytes per release-list entry); contents undefined on entry and exit.
+ * Gathers: on grids of at least 2^20 cells whose row pitch (4 * width bytes)
+ * and d_h are aligned to the device's texture pitch alignment (32 bytes on
+ * GB300), the particle kernel fetches each 2x2 footprint with one texture
+ * gather through a texture object that views d_h (clamp addressing, which
+ * is the i1, j1 clamp above; indices and weights computed as stated).  The
+ * object is created at the first call with that (d_h, width, height, device)
+ * and kept for the life of the process, so that a captured CUDA graph keeps
+ * a valid one; after 256 such buffers, further ones use plain loads.  Both
+ * fetch the same heights: results do not depend on the path.
  */
 size_t awo_simulate_workspace_bytes(uint32_t n_cells_max);
 awo_status awo_simulate(const float* d_h, awo_grid g, const uint32_t* d_cells,

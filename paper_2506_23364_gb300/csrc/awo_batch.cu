@@ -47,6 +47,7 @@ struct BatchReq {
     uint32_t starts_off;  // index of this request's first start record
     uint32_t texel;       // 1: the release list holds texels of the release texture
     TexelGeom tg;
+    cudaTextureObject_t tex;  // texture view of h for the footprint gathers, or 0 (loads)
 };
 
 struct BatchHeader {
@@ -87,6 +88,7 @@ struct ReqRegs {
     const TexelStart* starts;
     uint32_t k0, k1;
     bool texel;
+    cudaTextureObject_t tex;
 };
 
 __device__ __forceinline__ ReqRegs load_req(const BatchArgs& a, int r)
@@ -112,6 +114,7 @@ __device__ __forceinline__ ReqRegs load_req(const BatchArgs& a, int r)
     q.k0 = b.k0;
     q.k1 = b.k1;
     q.texel = b.texel != 0u;
+    q.tex = b.tex;
     return q;
 }
 
@@ -202,6 +205,7 @@ __global__ void __launch_bounds__(256) k_batch_starts(const __grid_constant__ Ba
 template <int THREADS, bool WARP_REFILL, bool TABLE_KEYS>
 __global__ void __launch_bounds__(THREADS) k_batch_simulate(const __grid_constant__ BatchArgs a)
 {
+    constexpr int kGather = 2;  // footprints by texture gather where the request has a view (AWO_MOVE_WORDS)
     __shared__ unsigned long long s_gp[AWO_BATCH_MAX + 1];
     const int n_req = (int)a.n_req;
     for (int i = threadIdx.x; i <= n_req; i += blockDim.x) s_gp[i] = a.hdr->chunk_prefix[i];
@@ -420,6 +424,7 @@ extern "C" awo_status awo_simulate_batched(const awo_sim_request* reqs, int32_t 
         b.tg.Wr = (uint32_t)wr;
         b.tg.n_tex = (uint32_t)(wr * hr);
         b.tg.scale = ldexpf(1.0f, -p->release_log2);
+        b.tex = dem_texture(q.d_h, q.grid);
         if (p->seed != reqs[0].params.seed) same_seed = false;
         if (p->flags & AWO_SIM_CLEAR_OUTPUTS) {
             const size_t bytes = (size_t)cells_of(q.grid) * sizeof(uint32_t);

@@ -82,4 +82,9 @@ inline bool sim_params_ok(const awo_sim_params* p, awo_grid g)
     return sim_params_ok(p, g.cell_size) && release_texture_dims(g, p->release_log2, &wr, &hr);
 }
 
+// Texture view of the DEM buffer d_h of grid g for the particle kernels'
+// footprint gathers, or 0 when the grid is small, the buffer or row pitch is
+// not texture-aligned, or the view table is full (awo_simulate.cu).
+cudaTextureObject_t dem_texture(const float* d_h, awo_grid g);
+
 }  // namespace awo

@@ -1,0 +1,59 @@
+"""The particle kernel's two ways of fetching a 2x2 footprint -- one texture
+gather through a texture object over the DEM (grids of at least 2^20 cells
+with a texture-aligned buffer and row pitch) and four loads (otherwise) --
+give the same rasters and statistics, equal to the oracle's, including
+particles that start on and run along the last row and column, where the
+footprint is clamped."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2506_23364_gb300 as awo
+from paper_2506_23364_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+H, W, CS = 1040, 1024, 10.0  # 1.06 M cells, row pitch 4096 B
+
+
+def _run(dh, cells, p):
+    g = awo.grid(W, H, CS)
+    count = torch.zeros((H, W), dtype=torch.int32, device="cuda")
+    maxe = torch.zeros((H, W), dtype=torch.float32, device="cuda")
+    stats = torch.zeros(6, dtype=torch.int64, device="cuda")
+    ws = torch.empty(awo.awo_simulate_workspace_bytes(cells.size), dtype=torch.uint8, device="cuda")
+    dc = torch.from_numpy(cells.view(np.int32)).cuda()
+    awo.awo_simulate(dh, g, dc, None, cells.size, p, count, maxe, stats, ws)
+    torch.cuda.synchronize()
+    return count.cpu().numpy().view(np.uint32), maxe.cpu().numpy(), awo.stats_dict(stats)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_texture_and_load_gathers_agree_with_the_oracle(seed):
+    # a DEM tilted towards the last row and column, so particles reach both borders
+    z = inputs.fbm(W + 16, 0.8, seed=40 + seed, relief=900.0)[:H, :W]
+    yy, xx = np.mgrid[0:H, 0:W]
+    h = (z + 3000.0 - 0.9 * CS * (yy + xx)).astype(np.float32)
+    rng = np.random.default_rng(seed)
+    border = np.concatenate([(H - 1) * W + rng.integers(0, W, 40), rng.integers(0, H, 40) * W + (W - 1),
+                             [H * W - 1, W - 1, (H - 1) * W, (H - 2) * W + W - 2]])
+    cells = np.unique(np.concatenate([rng.integers(0, H * W, 300), border])).astype(np.uint32)
+    op = oracle.SimParams(traj_per_cell=24, max_steps=1500, seed=(7 << 32) | seed)
+    p = awo.SimParams.make(traj_per_cell=24, max_steps=1500, seed=(7 << 32) | seed)
+    dh = torch.from_numpy(h).cuda()  # aligned: texture gathers
+    assert dh.data_ptr() % 32 == 0
+    buf = torch.zeros(H * W + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = dh.reshape(-1)
+    dh_off = buf[1:].view(H, W)  # 4 bytes off the texture alignment: loads
+    ca, ma, sa = _run(dh, cells, p)
+    cb, mb, sb = _run(dh_off, cells, p)
+    assert np.array_equal(ca, cb) and np.array_equal(ma, mb) and sa == sb
+    c64, rm, rst = oracle.simulate_threaded(h, CS, cells, op, threads=8)
+    assert np.array_equal(ca, oracle.counts_u32(c64))
+    assert np.array_equal(ma, rm)
+    for k in ("total_steps", "n_traj", "n_exited", "n_capped", "n_stopped"):
+        assert sa[k] == rst[k], k
+    # the border was reached: visits in the last row and column
+    assert ca[H - 1].sum() > 0 and ca[:, W - 1].sum() > 0
+    assert sa["n_exited"] > 0
