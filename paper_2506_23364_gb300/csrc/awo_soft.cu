@@ -46,6 +46,7 @@ struct SoftArgs {
     double* grad_theta;    // 2 (backward)
     double* grad_w;        // per release entry, FP64 scratch (backward)
     unsigned long long* stats;  // 6
+    cudaTextureObject_t tex;    // texture view of h for the footprint gathers (k_soft<_, true>), or 0
 };
 
 constexpr float SOFT_S_MIN = 1e-7f;
@@ -66,7 +67,8 @@ __global__ void __launch_bounds__(256) k_soft_starts(const __grid_constant__ Sof
 }
 
 // One soft particle.  GRAD = false: deposits; GRAD = true: gradient sums.
-template <bool GRAD>
+// TEX: footprints by texture gather through a.tex (else by loads).
+template <bool GRAD, bool TEX>
 __device__ __forceinline__ void soft_particle(const SoftArgs& a, uint32_t ci, uint32_t j, double& sum_mu,
                                               double& sum_k, unsigned long long& steps, bool& rejected)
 {
@@ -116,7 +118,7 @@ __device__ __forceinline__ void soft_particle(const SoftArgs& a, uint32_t ci, ui
         const float u1 = __fadd_rn(u, __fmul_rn(a.s, dx));
         const float v1 = __fadd_rn(v, __fmul_rn(a.s, dy));
         if (!(u1 >= 0.0f && u1 <= a.Wm1 && v1 >= 0.0f && v1 <= a.Hm1)) break;
-        const Foot f = gather(a.h, a.W, a.H, u1, v1);
+        const Foot f = foot_at<TEX ? 1 : 0>(a, u1, v1);
         const float z1 = bilinear(f, __fsub_rn(1.0f, f.fx), __fsub_rn(1.0f, f.fy));
         const float e1 = __fsub_rn(__fadd_rn(__fsub_rn(e, __fmul_rn(a.kD, e)), __fsub_rn(z, z1)), a.muD);
         const float sig = 1.0f / (1.0f + expf(-e1 * a.inv_tau));
@@ -172,7 +174,7 @@ __device__ __forceinline__ void soft_particle(const SoftArgs& a, uint32_t ci, ui
     }
 }
 
-template <bool GRAD>
+template <bool GRAD, bool TEX>
 __global__ void __launch_bounds__(128) k_soft(const __grid_constant__ SoftArgs a)
 {
     const uint64_t total = (uint64_t)soft_count(a) * a.N;
@@ -182,7 +184,7 @@ __global__ void __launch_bounds__(128) k_soft(const __grid_constant__ SoftArgs a
          t += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t ci = (uint32_t)(t / a.N), j = (uint32_t)(t - (uint64_t)ci * a.N);
         bool rejected = false;
-        soft_particle<GRAD>(a, ci, j, sum_mu, sum_k, steps, rejected);
+        soft_particle<GRAD, TEX>(a, ci, j, sum_mu, sum_k, steps, rejected);
         bad += rejected ? 1ull : 0ull;
         traj += rejected ? 0ull : 1ull;
     }
@@ -279,6 +281,7 @@ static awo_status soft_setup(SoftArgs& a, const float* d_h, awo_grid g, const ui
     a.starts = reinterpret_cast<CellStart*>(static_cast<char*>(d_ws) + SOFT_STARTS_OFF);
     a.grad_w = reinterpret_cast<double*>(static_cast<char*>(d_ws) + SOFT_STARTS_OFF +
                                          (size_t)n_cells_max * sizeof(CellStart));
+    a.tex = dem_texture(d_h, g);
     return AWO_OK;
 }
 
@@ -310,7 +313,10 @@ extern "C" awo_status awo_soft_forward(const float* d_h, awo_grid g, const uint3
         if (cudaMemsetAsync(d_deposit, 0, (size_t)cells_of(g) * sizeof(int64_t), s) != cudaSuccess) return AWO_ECUDA;
     if (a.N > 0 && n_cells_max > 0) {
         k_soft_starts<<<stream_blocks((int64_t)n_cells_max, 256), 256, 0, s>>>(a);
-        k_soft<false><<<soft_blocks(a), 128, 0, s>>>(a);
+        if (a.tex)
+            k_soft<false, true><<<soft_blocks(a), 128, 0, s>>>(a);
+        else
+            k_soft<false, false><<<soft_blocks(a), 128, 0, s>>>(a);
         st = launch_status();
         if (st != AWO_OK) return st;
     }
@@ -339,7 +345,10 @@ extern "C" awo_status awo_soft_backward(const float* d_h, awo_grid g, const uint
         return AWO_ECUDA;
     if (a.N > 0 && n_cells_max > 0) {
         k_soft_starts<<<stream_blocks((int64_t)n_cells_max, 256), 256, 0, s>>>(a);
-        k_soft<true><<<soft_blocks(a), 128, 0, s>>>(a);
+        if (a.tex)
+            k_soft<true, true><<<soft_blocks(a), 128, 0, s>>>(a);
+        else
+            k_soft<true, false><<<soft_blocks(a), 128, 0, s>>>(a);
     }
     if (n_cells_max > 0)
         k_to_float<<<stream_blocks((int64_t)n_cells_max, 256), 256, 0, s>>>(a.grad_w, n_cells_max, d_n_cells,

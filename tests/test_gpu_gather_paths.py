@@ -57,3 +57,39 @@ def test_texture_and_load_gathers_agree_with_the_oracle(seed):
     # the border was reached: visits in the last row and column
     assert ca[H - 1].sum() > 0 and ca[:, W - 1].sum() > 0
     assert sa["n_exited"] > 0
+
+
+def test_soft_forward_and_adjoint_same_on_both_paths():
+    """Soft deposits and their adjoint: the texture-gather and the load path
+    give the same fixed-point deposits and the same gradients."""
+    z = inputs.fbm(W + 16, 0.8, seed=44, relief=1500.0)[:H, :W]
+    h = (z + 2000.0).astype(np.float32)
+    rng = np.random.default_rng(3)
+    cells = np.unique(rng.integers(0, H * W, 500)).astype(np.uint32)
+    n = cells.size
+    p = awo.SimParams.make(traj_per_cell=16, max_steps=400, seed=11, drag_k=1e-3)
+    g = awo.grid(W, H, CS)
+    dc = torch.from_numpy(cells.view(np.int32)).cuda()
+    wt = torch.from_numpy(rng.uniform(0.5, 1.5, n).astype(np.float32)).cuda()
+    gd = torch.from_numpy(rng.normal(0, 1, (H, W)).astype(np.float32)).cuda()
+    dh = torch.from_numpy(h).cuda()
+    buf = torch.zeros(H * W + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = dh.reshape(-1)
+    out = []
+    for d in (dh, buf[1:].view(H, W)):
+        ws = torch.empty(awo.awo_soft_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+        dep = torch.zeros((H, W), dtype=torch.int64, device="cuda")
+        st = torch.zeros(6, dtype=torch.int64, device="cuda")
+        awo.awo_soft_forward(d, g, dc, None, n, wt, p, 1.0, dep, st, ws)
+        gt = torch.zeros(2, dtype=torch.float64, device="cuda")
+        gw = torch.zeros(n, dtype=torch.float32, device="cuda")
+        awo.awo_soft_backward(d, g, dc, None, n, wt, p, 1.0, gd, gt, gw, ws)
+        torch.cuda.synchronize()
+        out.append((dep.cpu().numpy(), st.cpu().numpy(), gt.cpu().numpy(), gw.cpu().numpy()))
+    (da, sa, ga, wa), (db, sb, gb, wb) = out
+    assert np.array_equal(da, db) and np.array_equal(sa, sb)
+    # the gradients are FP64 sums of per-particle FP32 terms, added in atomic
+    # order: equal up to that order's rounding
+    assert np.allclose(wa, wb, rtol=1e-6, atol=0.0)
+    assert np.allclose(ga, gb, rtol=1e-9, atol=0.0)
+    assert int(sa[0]) > 0 and int(da.sum()) > 0
