@@ -243,8 +243,11 @@ awo_status awo_release_noalloc(const float* d_tan2, awo_grid g, double slope_lo_
  * is the i1, j1 clamp above; indices and weights computed as stated).  The
  * object is created at the first call with that (d_h, width, height, device)
  * and kept for the life of the process, so that a captured CUDA graph keeps
- * a valid one; after 256 such buffers, further ones use plain loads.  Both
- * fetch the same heights: results do not depend on the path.
+ * a valid one; after 256 such buffers, further ones use plain loads, and a
+ * call made while `stream` is being captured creates none (it uses an
+ * existing view, else the loads).  Both fetch the same heights: results do
+ * not depend on the path.  The same holds for awo_simulate_batched (per
+ * request) and the soft-deposit calls.
  */
 size_t awo_simulate_workspace_bytes(uint32_t n_cells_max);
 awo_status awo_simulate(const float* d_h, awo_grid g, const uint32_t* d_cells,

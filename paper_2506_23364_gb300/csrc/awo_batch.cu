@@ -424,7 +424,7 @@ extern "C" awo_status awo_simulate_batched(const awo_sim_request* reqs, int32_t 
         b.tg.Wr = (uint32_t)wr;
         b.tg.n_tex = (uint32_t)(wr * hr);
         b.tg.scale = ldexpf(1.0f, -p->release_log2);
-        b.tex = dem_texture(q.d_h, q.grid);
+        b.tex = dem_texture(q.d_h, q.grid, s);
         if (p->seed != reqs[0].params.seed) same_seed = false;
         if (p->flags & AWO_SIM_CLEAR_OUTPUTS) {
             const size_t bytes = (size_t)cells_of(q.grid) * sizeof(uint32_t);

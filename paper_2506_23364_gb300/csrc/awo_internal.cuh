@@ -84,7 +84,8 @@ inline bool sim_params_ok(const awo_sim_params* p, awo_grid g)
 
 // Texture view of the DEM buffer d_h of grid g for the particle kernels'
 // footprint gathers, or 0 when the grid is small, the buffer or row pitch is
-// not texture-aligned, or the view table is full (awo_simulate.cu).
-cudaTextureObject_t dem_texture(const float* d_h, awo_grid g);
+// not texture-aligned, the view table is full, or a new view would be needed
+// while stream s is capturing (awo_simulate.cu).
+cudaTextureObject_t dem_texture(const float* d_h, awo_grid g, cudaStream_t s);
 
 }  // namespace awo

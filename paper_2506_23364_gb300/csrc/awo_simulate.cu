@@ -223,7 +223,10 @@ static int sim_blocks_per_sm()
 // path), so that a graph that captured a launch keeps a valid view.  A view
 // needs the row pitch and the base address aligned to the device's texture
 // pitch alignment and a grid within the 2D pitch-linear texture limits;
-// otherwise (or if creation fails) the kernel gathers with loads.  Grids
+// otherwise (or if creation fails) the kernel gathers with loads.  While the
+// launch stream is being captured into a graph no view is created (an
+// existing one is used, else the loads), so a capture never sees a call it
+// might refuse.  Grids
 // under DEM_VIEW_MIN_CELLS take the loads too: measured on GB300 (particle
 // kernel, texture gathers against loads), 8192^2 -5.5%, 2048^2 -1%, 256^2
 // +4% (a DEM that small stays in L1, where the loads' latency is shorter).
@@ -236,7 +239,7 @@ struct DemView {
     cudaTextureObject_t tex;
 };
 
-cudaTextureObject_t dem_texture(const float* d_h, awo_grid g)
+cudaTextureObject_t dem_texture(const float* d_h, awo_grid g, cudaStream_t s)
 {
     if (cells_of(g) < DEM_VIEW_MIN_CELLS) return 0;
     static std::mutex mu;
@@ -249,6 +252,11 @@ cudaTextureObject_t dem_texture(const float* d_h, awo_grid g)
         if (views[i].h == d_h && views[i].W == g.width && views[i].H == g.height && views[i].dev == dev)
             return views[i].tex;
     if (n_views == DEM_VIEWS_MAX) return 0;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return 0;
+    }
     int pitch_align = 0, max_w = 0, max_h = 0;
     if (cudaDeviceGetAttribute(&pitch_align, cudaDevAttrTexturePitchAlignment, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&max_w, cudaDevAttrMaxTexture2DLinearWidth, dev) != cudaSuccess ||
@@ -350,7 +358,7 @@ extern "C" awo_status awo_simulate(const float* d_h, awo_grid g, const uint32_t*
     a.tg.scale = ldexpf(1.0f, -p->release_log2);
     const bool texels = p->release_log2 != 0;
 
-    a.tex = dem_texture(d_h, g);
+    a.tex = dem_texture(d_h, g, s);
 
     if (a.N > 0 && (n_cells_max > 0)) {
         const unsigned pro_blocks = stream_blocks((int64_t)n_cells_max, 256);

@@ -238,7 +238,7 @@ static size_t soft_ws_bytes(uint32_t n_cells_max)
 
 static awo_status soft_setup(SoftArgs& a, const float* d_h, awo_grid g, const uint32_t* d_cells,
                              const uint32_t* d_n_cells, uint32_t n_cells_max, const float* d_weight,
-                             const awo_sim_params* p, float tau, void* d_ws, size_t ws_bytes)
+                             const awo_sim_params* p, float tau, void* d_ws, size_t ws_bytes, cudaStream_t s)
 {
     if (!d_h || !d_ws || !grid_ok(g) || !sim_params_ok(p, g.cell_size) || p->release_log2 != 0) return AWO_EINVAL;
     if (n_cells_max > 0 && (!d_cells || !d_weight)) return AWO_EINVAL;
@@ -281,7 +281,7 @@ static awo_status soft_setup(SoftArgs& a, const float* d_h, awo_grid g, const ui
     a.starts = reinterpret_cast<CellStart*>(static_cast<char*>(d_ws) + SOFT_STARTS_OFF);
     a.grad_w = reinterpret_cast<double*>(static_cast<char*>(d_ws) + SOFT_STARTS_OFF +
                                          (size_t)n_cells_max * sizeof(CellStart));
-    a.tex = dem_texture(d_h, g);
+    a.tex = dem_texture(d_h, g, s);
     return AWO_OK;
 }
 
@@ -303,7 +303,8 @@ extern "C" awo_status awo_soft_forward(const float* d_h, awo_grid g, const uint3
                                        awo_sim_stats* d_stats, void* d_ws, size_t ws_bytes, void* stream)
 {
     SoftArgs a;
-    awo_status st = soft_setup(a, d_h, g, d_cells, d_n_cells, n_cells_max, d_weight, p, tau, d_ws, ws_bytes);
+    awo_status st =
+        soft_setup(a, d_h, g, d_cells, d_n_cells, n_cells_max, d_weight, p, tau, d_ws, ws_bytes, as_stream(stream));
     if (st != AWO_OK) return st;
     if (!d_deposit || (((uintptr_t)d_deposit) & 7u) != 0) return AWO_EINVAL;
     a.deposit = reinterpret_cast<unsigned long long*>(d_deposit);
@@ -333,7 +334,8 @@ extern "C" awo_status awo_soft_backward(const float* d_h, awo_grid g, const uint
                                         void* stream)
 {
     SoftArgs a;
-    awo_status st = soft_setup(a, d_h, g, d_cells, d_n_cells, n_cells_max, d_weight, p, tau, d_ws, ws_bytes);
+    awo_status st =
+        soft_setup(a, d_h, g, d_cells, d_n_cells, n_cells_max, d_weight, p, tau, d_ws, ws_bytes, as_stream(stream));
     if (st != AWO_OK) return st;
     if (!d_grad_deposit || !d_grad_theta || (n_cells_max > 0 && !d_grad_weight)) return AWO_EINVAL;
     a.grad = d_grad_deposit;

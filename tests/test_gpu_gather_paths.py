@@ -93,3 +93,32 @@ def test_soft_forward_and_adjoint_same_on_both_paths():
     assert np.allclose(wa, wb, rtol=1e-6, atol=0.0)
     assert np.allclose(ga, gb, rtol=1e-9, atol=0.0)
     assert int(sa[0]) > 0 and int(da.sum()) > 0
+
+
+def test_first_use_of_a_buffer_inside_a_graph_capture():
+    """A DEM buffer whose first particle call is being captured into a CUDA
+    graph gets no new texture view (the capture must not see a call it could
+    refuse): the graph runs with loads and gives the same rasters as a plain
+    call, which then creates the view and gathers through it."""
+    z = inputs.fbm(W + 16, 0.8, seed=45, relief=1200.0)[:H, :W]
+    h = (z + 1500.0).astype(np.float32)
+    rng = np.random.default_rng(9)
+    cells = np.unique(rng.integers(0, H * W, 200)).astype(np.uint32)
+    p = awo.SimParams.make(traj_per_cell=16, max_steps=500, seed=3, flags=1)  # clear the rasters first
+    g = awo.grid(W, H, CS)
+    dh = torch.from_numpy(h).cuda()  # a buffer no call has seen
+    dc = torch.from_numpy(cells.view(np.int32)).cuda()
+    count = torch.zeros((H, W), dtype=torch.int32, device="cuda")
+    maxe = torch.zeros((H, W), dtype=torch.float32, device="cuda")
+    stats = torch.zeros(6, dtype=torch.int64, device="cuda")
+    ws = torch.empty(awo.awo_simulate_workspace_bytes(cells.size), dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        awo.awo_simulate(dh, g, dc, None, cells.size, p, count, maxe, stats, ws)
+    graph.replay()
+    torch.cuda.synchronize()
+    cg, mg, sg = count.cpu().numpy().view(np.uint32).copy(), maxe.cpu().numpy().copy(), awo.stats_dict(stats)
+    cp, mp, sp = _run(dh, cells, p)
+    assert np.array_equal(cg, cp) and np.array_equal(mg, mp) and sg == sp
+    assert sg["total_steps"] > 0
