@@ -217,7 +217,8 @@ static int sim_blocks_per_sm()
 }
 
 // Texture views of DEM buffers for the gathers of k_simulate: a texture
-// object is a descriptor of (address, width, height, row pitch) -- no copy --
+// object is a descriptor of (address, width, height, row pitch) -- no copy;
+// the words are viewed as 32-bit unsigned texels, returned bit for bit --
 // created on the first call with a buffer and kept for the life of the
 // process (at most DEM_VIEWS_MAX of them; further buffers take the load
 // path), so that a graph that captured a launch keeps a valid view.  A view
@@ -270,7 +271,7 @@ cudaTextureObject_t dem_texture(const float* d_h, awo_grid g, cudaStream_t s)
     memset(&rd, 0, sizeof(rd));
     rd.resType = cudaResourceTypePitch2D;
     rd.res.pitch2D.devPtr = const_cast<float*>(d_h);
-    rd.res.pitch2D.desc = cudaCreateChannelDesc<float>();
+    rd.res.pitch2D.desc = cudaCreateChannelDesc<unsigned int>();  // raw words: no subnormal flush
     rd.res.pitch2D.width = (size_t)g.width;
     rd.res.pitch2D.height = (size_t)g.height;
     rd.res.pitch2D.pitchInBytes = pitch;

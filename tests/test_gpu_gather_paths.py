@@ -122,3 +122,31 @@ def test_first_use_of_a_buffer_inside_a_graph_capture():
     cp, mp, sp = _run(dh, cells, p)
     assert np.array_equal(cg, cp) and np.array_equal(mg, mp) and sg == sp
     assert sg["total_steps"] > 0
+
+
+def test_subnormal_heights_read_exactly():
+    """Heights in the FP32 subnormal range reach the arithmetic unchanged on
+    both paths (the texture view returns the DEM's words as raw bits, with
+    no flush to zero), so the rasters -- energies in the subnormal range
+    included -- equal the oracle's."""
+    z = inputs.fbm(W + 16, 0.8, seed=46, relief=1.0)[:H, :W]
+    z = (z - z.min()) / (z.max() - z.min())
+    h = (z * 2.0 ** -125).astype(np.float32)  # about half below 2^-126 (subnormal)
+    tiny = np.finfo(np.float32).tiny
+    assert 0.1 < float(np.mean((h > 0) & (h < tiny))) < 0.9
+    rng = np.random.default_rng(12)
+    cells = np.unique(rng.integers(0, H * W, 400)).astype(np.uint32)
+    kw = dict(traj_per_cell=8, max_steps=300, seed=13, mu=0.0)
+    op = oracle.SimParams(**kw)
+    p = awo.SimParams.make(**kw)
+    dh = torch.from_numpy(h).cuda()
+    buf = torch.zeros(H * W + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = dh.reshape(-1)
+    ca, ma, sa = _run(dh, cells, p)
+    cb, mb, sb = _run(buf[1:].view(H, W), cells, p)
+    assert np.array_equal(ca, cb) and np.array_equal(ma, mb) and sa == sb
+    c64, rm, rst = oracle.simulate_threaded(h, CS, cells, op, threads=8)
+    assert np.array_equal(ca, oracle.counts_u32(c64))
+    assert np.array_equal(ma.view(np.uint32), rm.view(np.uint32))
+    assert sa["total_steps"] == rst["total_steps"] and sa["total_steps"] > 0
+    assert np.any((ma > 0) & (ma < tiny))  # energies recorded in the subnormal range
