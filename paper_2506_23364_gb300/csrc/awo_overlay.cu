@@ -9,16 +9,31 @@
 namespace awo {
 
 // vel = sqrt((2 g) maxe); float4 loads and stores when both rasters are
-// 16-byte aligned, then a scalar tail.
+// 16-byte aligned, then a scalar tail.  A thread issues the loads of
+// STREAM_UNROLL float4 (each coalesced across the grid) before their stores,
+// so that enough bytes are in flight per SM to keep HBM busy.
+constexpr int STREAM_UNROLL = 4;
+
 __global__ void k_finalize(const float* __restrict__ maxe, int64_t n, float g2, float* __restrict__ vel, bool vec4)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t n4 = vec4 ? n / 4 : 0;
-    for (int64_t q = tid; q < n4; q += stride) {
-        const float4 m = __ldg(reinterpret_cast<const float4*>(maxe) + q);
-        reinterpret_cast<float4*>(vel)[q] = make_float4(__fsqrt_rn(__fmul_rn(g2, m.x)), __fsqrt_rn(__fmul_rn(g2, m.y)),
-                                                        __fsqrt_rn(__fmul_rn(g2, m.z)), __fsqrt_rn(__fmul_rn(g2, m.w)));
+    for (int64_t q = tid; q < n4; q += STREAM_UNROLL * stride) {
+        float4 m[STREAM_UNROLL];
+#pragma unroll
+        for (int u = 0; u < STREAM_UNROLL; ++u) {
+            const int64_t k = q + u * stride;
+            m[u] = k < n4 ? __ldg(reinterpret_cast<const float4*>(maxe) + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < STREAM_UNROLL; ++u) {
+            const int64_t k = q + u * stride;
+            if (k < n4)
+                reinterpret_cast<float4*>(vel)[k] =
+                    make_float4(__fsqrt_rn(__fmul_rn(g2, m[u].x)), __fsqrt_rn(__fmul_rn(g2, m[u].y)),
+                                __fsqrt_rn(__fmul_rn(g2, m[u].z)), __fsqrt_rn(__fmul_rn(g2, m[u].w)));
+        }
     }
     for (int64_t i = 4 * n4 + tid; i < n; i += stride) vel[i] = __fsqrt_rn(__fmul_rn(g2, maxe[i]));
 }

@@ -36,17 +36,32 @@ int sm_count()
 // ---------------------------------------------------------------------------
 // Four heights per thread (8-byte load, float4 store) when both buffers allow
 // it, then a scalar tail.
+// A thread issues the loads of DECODE_UNROLL groups of four heights (each
+// coalesced across the grid) before their stores, so that enough bytes are
+// in flight per SM to keep HBM busy.
+constexpr int DECODE_UNROLL = 4;
+
 __global__ void k_decode_u16(const uint16_t* __restrict__ q, int64_t n, float scale, float* __restrict__ h, bool vec4)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t n4 = vec4 ? n / 4 : 0;
-    for (int64_t k = tid; k < n4; k += stride) {
-        const uint2 w = __ldg(reinterpret_cast<const uint2*>(q) + k);
-        reinterpret_cast<float4*>(h)[k] = make_float4(__fmul_rn(__uint2float_rn(w.x & 0xffffu), scale),
-                                                      __fmul_rn(__uint2float_rn(w.x >> 16), scale),
-                                                      __fmul_rn(__uint2float_rn(w.y & 0xffffu), scale),
-                                                      __fmul_rn(__uint2float_rn(w.y >> 16), scale));
+    for (int64_t k0 = tid; k0 < n4; k0 += DECODE_UNROLL * stride) {
+        uint2 w[DECODE_UNROLL];
+#pragma unroll
+        for (int u = 0; u < DECODE_UNROLL; ++u) {
+            const int64_t k = k0 + u * stride;
+            w[u] = k < n4 ? __ldg(reinterpret_cast<const uint2*>(q) + k) : make_uint2(0u, 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < DECODE_UNROLL; ++u) {
+            const int64_t k = k0 + u * stride;
+            if (k < n4)
+                reinterpret_cast<float4*>(h)[k] = make_float4(__fmul_rn(__uint2float_rn(w[u].x & 0xffffu), scale),
+                                                              __fmul_rn(__uint2float_rn(w[u].x >> 16), scale),
+                                                              __fmul_rn(__uint2float_rn(w[u].y & 0xffffu), scale),
+                                                              __fmul_rn(__uint2float_rn(w[u].y >> 16), scale));
+        }
     }
     for (int64_t i = 4 * n4 + tid; i < n; i += stride) h[i] = __fmul_rn(__uint2float_rn((unsigned)q[i]), scale);
 }
