@@ -324,8 +324,10 @@ def run_awo(args, R: Ranks):
     torch.cuda.synchronize()
     st = ov.stats_dict()
     visits = st["total_steps"] + st["n_traj"]
-    # decode, normals, release (mask, scan, scatter), particle prologue and kernel, finalize, mipmap levels
-    launches_per_step = (1 if w.quantised else 0) + 1 + 3 + 2 + 1 + max(w.lod_levels - 1, 0)
+    # decode, normals, release (mask, scan, scatter), particle prologue and kernel, finalize, mipmap
+    # (levels 1..6 in one launch, one launch per further level)
+    lod_launches = 0 if w.lod_levels <= 1 else 1 + max(w.lod_levels - 1 - 6, 0)
+    launches_per_step = (1 if w.quantised else 0) + 1 + 3 + 2 + 1 + lod_launches
 
     peaks_probe = _probe_peaks(torch, awo)
     clocks = ClockSampler(R.local)

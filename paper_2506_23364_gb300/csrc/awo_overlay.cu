@@ -4,6 +4,8 @@
 // reduces 2x2 blocks of the level above (two output texels from 16-byte rows
 // when the level allows it; counts summed in 64 bits and saturated,
 // velocities by max), so every level reads its parent once.
+#include <string.h>
+
 #include "awo_internal.cuh"
 
 namespace awo {
@@ -94,6 +96,121 @@ __global__ void k_lod_level(const uint32_t* __restrict__ c_in, const float* __re
     }
 }
 
+// Levels 1 .. 1 + LOD_FUSED - 1 of the mipmap in one pass over level 0.  A
+// block owns a 32 x 32 tile of level 1 (a 64 x 64 tile of level 0) and all
+// its descendants: 16 x 16 of level 2, ... 1 x 1 of level 6, since the tiles
+// of every level nest.  Level 1 is reduced from level 0 in global memory,
+// each further level from the previous one in shared memory; every texel is
+// the saturating count sum and the velocity maximum of its existing children
+// (children past a level's edge are ignored), as in k_lod_level.  One read of
+// level 0 and one write of each level, instead of a read and a write per
+// level with a launch each.
+constexpr int LOD_TILE = 32;   // level-1 tile side
+constexpr int LOD_FUSED = 6;   // levels a block can finish: 32, 16, 8, 4, 2, 1
+
+struct LodArgs {
+    const uint32_t* c0;
+    const float* v0;
+    int w[LOD_FUSED + 1], h[LOD_FUSED + 1];  // level sizes 0 .. LOD_FUSED
+    uint32_t* c[LOD_FUSED];                  // outputs of levels 1 .. LOD_FUSED
+    float* v[LOD_FUSED];
+    int n_out;                               // levels written, 1 .. LOD_FUSED
+    bool vec2;                               // level-0 child pairs as uint2 / float2
+};
+
+__global__ void __launch_bounds__(256) k_lod_fused(const __grid_constant__ LodArgs a)
+{
+    __shared__ uint32_t sc[2][LOD_TILE][LOD_TILE + 1];
+    __shared__ float sv[2][LOD_TILE][LOD_TILE + 1];
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    const int bx = blockIdx.x, by = blockIdx.y;
+    // level 1 from level 0: four texels per thread, rows ty, ty + 8, ...
+    {
+        const int w0 = a.w[0], h0 = a.h[0], w1 = a.w[1], h1 = a.h[1];
+        const int X = bx * LOD_TILE + tx;
+#pragma unroll
+        for (int k = 0; k < LOD_TILE / 8; ++k) {
+            const int y = ty + 8 * k, Y = by * LOD_TILE + y;
+            if (X < w1 && Y < h1) {
+                const int sx = 2 * X, sy = 2 * Y;
+                const bool hx = sx + 1 < w0, hy = sy + 1 < h0;
+                const uint32_t r0 = (uint32_t)sy * (uint32_t)w0 + (uint32_t)sx, r1 = r0 + (uint32_t)w0;
+                unsigned long long sum;
+                float m;
+                if (a.vec2) {  // w0 even: both columns exist and the pair is 8-byte aligned
+                    const uint2 c_0 = __ldg(reinterpret_cast<const uint2*>(a.c0 + r0));
+                    const float2 v_0 = __ldg(reinterpret_cast<const float2*>(a.v0 + r0));
+                    sum = (unsigned long long)c_0.x + c_0.y;
+                    m = fmaxf(v_0.x, v_0.y);
+                    if (hy) {
+                        const uint2 c_1 = __ldg(reinterpret_cast<const uint2*>(a.c0 + r1));
+                        const float2 v_1 = __ldg(reinterpret_cast<const float2*>(a.v0 + r1));
+                        sum += (unsigned long long)c_1.x + c_1.y;
+                        m = fmaxf(m, fmaxf(v_1.x, v_1.y));
+                    }
+                } else {
+                    sum = __ldg(a.c0 + r0);
+                    m = __ldg(a.v0 + r0);
+                    if (hx) {
+                        sum += __ldg(a.c0 + r0 + 1);
+                        m = fmaxf(m, __ldg(a.v0 + r0 + 1));
+                    }
+                    if (hy) {
+                        sum += __ldg(a.c0 + r1);
+                        m = fmaxf(m, __ldg(a.v0 + r1));
+                        if (hx) {
+                            sum += __ldg(a.c0 + r1 + 1);
+                            m = fmaxf(m, __ldg(a.v0 + r1 + 1));
+                        }
+                    }
+                }
+                const uint32_t c = sum > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)sum;
+                const uint32_t o = (uint32_t)Y * (uint32_t)w1 + (uint32_t)X;
+                a.c[0][o] = c;
+                a.v[0][o] = m;
+                sc[0][y][tx] = c;
+                sv[0][y][tx] = m;
+            }
+        }
+    }
+    // levels 2 .. n_out from the previous level in shared memory
+    int t = LOD_TILE, src = 0;
+    for (int l = 2; l <= a.n_out; ++l) {
+        __syncthreads();
+        const int t2 = t >> 1;
+        if (tid < t2 * t2) {
+            const int x = tid % t2, y = tid / t2;
+            const int X = bx * t2 + x, Y = by * t2 + y;
+            if (X < a.w[l] && Y < a.h[l]) {
+                const int wp = a.w[l - 1], hp = a.h[l - 1];
+                const bool hx = 2 * X + 1 < wp, hy = 2 * Y + 1 < hp;
+                unsigned long long sum = sc[src][2 * y][2 * x];
+                float m = sv[src][2 * y][2 * x];
+                if (hx) {
+                    sum += sc[src][2 * y][2 * x + 1];
+                    m = fmaxf(m, sv[src][2 * y][2 * x + 1]);
+                }
+                if (hy) {
+                    sum += sc[src][2 * y + 1][2 * x];
+                    m = fmaxf(m, sv[src][2 * y + 1][2 * x]);
+                    if (hx) {
+                        sum += sc[src][2 * y + 1][2 * x + 1];
+                        m = fmaxf(m, sv[src][2 * y + 1][2 * x + 1]);
+                    }
+                }
+                const uint32_t c = sum > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)sum;
+                const uint32_t o = (uint32_t)Y * (uint32_t)a.w[l] + (uint32_t)X;
+                a.c[l - 1][o] = c;
+                a.v[l - 1][o] = m;
+                sc[src ^ 1][y][x] = c;
+                sv[src ^ 1][y][x] = m;
+            }
+        }
+        src ^= 1;
+        t = t2;
+    }
+}
+
 }  // namespace awo
 
 using namespace awo;
@@ -119,7 +236,33 @@ extern "C" awo_status awo_overlay_lod(const uint32_t* d_count, const float* d_ve
     const uint32_t* ci = d_count;
     const float* vi = d_vel;
     int w = g.width, h = g.height;
-    for (int l = 1; l < levels; ++l) {
+    int l = 1;
+    if (levels > 1) {  // levels 1 .. up to LOD_FUSED in one launch
+        LodArgs a;
+        memset(&a, 0, sizeof(a));
+        a.c0 = d_count;
+        a.v0 = d_vel;
+        a.n_out = levels - 1 < LOD_FUSED ? levels - 1 : LOD_FUSED;
+        a.w[0] = g.width;
+        a.h[0] = g.height;
+        for (int k = 1; k <= a.n_out; ++k) {
+            a.w[k] = (a.w[k - 1] + 1) / 2;
+            a.h[k] = (a.h[k - 1] + 1) / 2;
+            a.c[k - 1] = d_count_lv[k - 1];
+            a.v[k - 1] = d_vel_lv[k - 1];
+        }
+        a.vec2 = g.width % 2 == 0 && ((((uintptr_t)d_count) | ((uintptr_t)d_vel)) & 7u) == 0;
+        const dim3 grid((unsigned)((a.w[1] + LOD_TILE - 1) / LOD_TILE), (unsigned)((a.h[1] + LOD_TILE - 1) / LOD_TILE));
+        k_lod_fused<<<grid, 256, 0, s>>>(a);
+        awo_status st = launch_status();
+        if (st != AWO_OK) return st;
+        l = 1 + a.n_out;
+        ci = d_count_lv[a.n_out - 1];
+        vi = d_vel_lv[a.n_out - 1];
+        w = a.w[a.n_out];
+        h = a.h[a.n_out];
+    }
+    for (; l < levels; ++l) {
         int w2 = (w + 1) / 2, h2 = (h + 1) / 2;
         const bool vec = w % 4 == 0 && h % 2 == 0 && ((((uintptr_t)ci) | ((uintptr_t)vi)) & 15u) == 0 &&
                          ((((uintptr_t)d_count_lv[l - 1]) | ((uintptr_t)d_vel_lv[l - 1])) & 7u) == 0;
