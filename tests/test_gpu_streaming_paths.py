@@ -86,7 +86,8 @@ def test_release_paths(shape, offset, with_mask):
 
 
 @pytest.mark.parametrize("shape,levels", [((64, 128), 6), ((66, 132), 5), ((33, 257), 5), ((8, 4), 3),
-                                          ((2, 8), 3), ((512, 512), 9)])
+                                          ((2, 8), 3), ((512, 512), 9), ((777, 1000), 11), ((1, 700), 11),
+                                          ((130, 2), 8)])
 @pytest.mark.parametrize("offset", [0, 1])
 def test_finalize_lod_paths(shape, levels, offset):
     H, W = shape
