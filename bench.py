@@ -324,10 +324,10 @@ def run_awo(args, R: Ranks):
     torch.cuda.synchronize()
     st = ov.stats_dict()
     visits = st["total_steps"] + st["n_traj"]
-    # decode, normals, release (mask, scan, scatter), particle prologue and kernel, finalize, mipmap
-    # (levels 1..6 in one launch, one launch per further level)
-    lod_launches = 0 if w.lod_levels <= 1 else 1 + max(w.lod_levels - 1 - 6, 0)
-    launches_per_step = (1 if w.quantised else 0) + 1 + 3 + 2 + 1 + lod_launches
+    # decode, normals, release (mask, scan, scatter), particle prologue and kernel, then velocity and
+    # mipmap: one launch for both and levels 1..6, one per further level (velocity alone without a mipmap)
+    lod_launches = 1 if w.lod_levels <= 1 else 1 + max(w.lod_levels - 1 - 6, 0)
+    launches_per_step = (1 if w.quantised else 0) + 1 + 3 + 2 + lod_launches
 
     peaks_probe = _probe_peaks(torch, awo)
     clocks = ClockSampler(R.local)
@@ -729,6 +729,8 @@ def run_stages(args, R: Ranks):
         ("finalize", lambda: awo.awo_finalize(ov.maxe, g, 9.81, ov.vel), 8 * n),
         ("mipmap (5 levels)", lambda: awo.awo_overlay_lod(ov.count, ov.vel, g, w.lod_levels, ov.count_lv, ov.vel_lv),
          8 * n + lv_bytes),
+        ("finalize + mipmap (one pass)", lambda: awo.awo_finalize_lod(ov.maxe, ov.count, g, 9.81, w.lod_levels, ov.vel,
+                                                                      ov.count_lv, ov.vel_lv), 12 * n + lv_bytes),
         ("compose over base", lambda: awo.awo_compose(ov.vel, ov.count, g, cm, base, rgba), 16 * n),
         ("snow cover (alpha + rgba)", lambda: awo.awo_snow_cover(ov.h, nz, g, sp, alpha, rgba), 16 * n),
     ]

@@ -385,6 +385,17 @@ awo_status awo_overlay_lod(const uint32_t* d_count, const float* d_vel, awo_grid
                            uint32_t* const* d_count_lv, float* const* d_vel_lv, void* stream);
 
 /*
+ * c' + d in one pass: exactly awo_finalize(d_maxe, g, gravity, d_vel)
+ * followed by awo_overlay_lod(d_count, d_vel, g, levels, ...), but level 0's
+ * velocity is made from d_maxe as the mipmap reads it, so the velocity
+ * raster is written once and never read back.  d_vel may alias d_maxe.
+ * Arguments, ranges and errors as in the two calls.
+ */
+awo_status awo_finalize_lod(const float* d_maxe, const uint32_t* d_count, awo_grid g, float gravity,
+                            int32_t levels, float* d_vel, uint32_t* const* d_count_lv, float* const* d_vel_lv,
+                            void* stream);
+
+/*
  * Compose (Sec. 3: the compose pass alpha-blends the data-driven overlay over
  * the base map; Fig. 4: colour encodes Z^delta_max, read as velocity).
  * Exact.  Per texel: x = d_value[i] clamped to [value[0], value[n_stops-1]];

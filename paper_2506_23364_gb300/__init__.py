@@ -136,6 +136,7 @@ def lib() -> ctypes.CDLL:
         "awo_simulate": (st, [vp, Grid, vp, vp, u32, ctypes.POINTER(SimParams), vp, vp, vp, vp, sz, vp]),
         "awo_finalize": (st, [vp, Grid, f32, vp, vp]),
         "awo_overlay_lod": (st, [vp, vp, Grid, i32, vp, vp, vp]),
+        "awo_finalize_lod": (st, [vp, vp, Grid, f32, i32, vp, vp, vp, vp]),
         "awo_simulate_batched_workspace_bytes": (sz, [vp, i32]),
         "awo_simulate_batched": (st, [vp, i32, vp, vp, vp, sz, vp]),
         "awo_tune_batched": (st, [vp, i32, vp, sz, vp, vp, vp]),
@@ -443,8 +444,7 @@ def lod_shapes(g: Grid, levels: int) -> list[tuple[int, int]]:
     return out
 
 
-def awo_overlay_lod(count: torch.Tensor, vel: torch.Tensor, g: Grid, levels: int, count_lv: list, vel_lv: list,
-                    stream=None):
+def _lod_pointers(g: Grid, levels: int, count_lv: list, vel_lv: list):
     shapes = lod_shapes(g, levels)
     if len(count_lv) != levels - 1 or len(vel_lv) != levels - 1:
         raise ValueError("count_lv / vel_lv need levels-1 tensors")
@@ -458,9 +458,25 @@ def awo_overlay_lod(count: torch.Tensor, vel: torch.Tensor, g: Grid, levels: int
             raise TypeError("count_lv tensors must be int32 or uint32")
         cp[l - 1] = _dev(cl, cl.dtype, hh * ww, f"count_lv[{l - 1}]")
         vp[l - 1] = _dev(vl, torch.float32, hh * ww, f"vel_lv[{l - 1}]")
+    return (cp, vp) if levels > 1 else (None, None)
+
+
+def awo_overlay_lod(count: torch.Tensor, vel: torch.Tensor, g: Grid, levels: int, count_lv: list, vel_lv: list,
+                    stream=None):
+    cp, vp = _lod_pointers(g, levels, count_lv, vel_lv)
     _check(lib().awo_overlay_lod(_dev(count, count.dtype, g.cells, "count"), _dev(vel, torch.float32, g.cells, "vel"),
-                                 g, int(levels), cp if levels > 1 else None, vp if levels > 1 else None,
-                                 _stream(stream)), "awo_overlay_lod")
+                                 g, int(levels), cp, vp, _stream(stream)), "awo_overlay_lod")
+
+
+def awo_finalize_lod(maxe: torch.Tensor, count: torch.Tensor, g: Grid, gravity: float, levels: int,
+                     vel: torch.Tensor, count_lv: list, vel_lv: list, stream=None):
+    """awo_finalize then awo_overlay_lod in one pass (see awo.h)."""
+    if count.dtype not in (torch.int32, torch.uint32):
+        raise TypeError("count must be int32 or uint32")
+    cp, vp = _lod_pointers(g, levels, count_lv, vel_lv)
+    _check(lib().awo_finalize_lod(_dev(maxe, torch.float32, g.cells, "maxe"), _dev(count, count.dtype, g.cells, "count"),
+                                  g, gravity, int(levels), _dev(vel, torch.float32, g.cells, "vel"), cp, vp,
+                                  _stream(stream)), "awo_finalize_lod")
 
 
 def awo_probe_threads() -> int:

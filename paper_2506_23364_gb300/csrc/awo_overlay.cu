@@ -104,13 +104,18 @@ __global__ void k_lod_level(const uint32_t* __restrict__ c_in, const float* __re
 // the saturating count sum and the velocity maximum of its existing children
 // (children past a level's edge are ignored), as in k_lod_level.  One read of
 // level 0 and one write of each level, instead of a read and a write per
-// level with a launch each.
+// level with a launch each.  FROM_MAXE: level 0's velocity is not read but
+// made from the maximum energy as it is needed, vel = sqrt((2 g) maxe), and
+// written (awo_finalize fused in): each level-0 cell is the child of exactly
+// one level-1 texel, so each is computed and written once.
 constexpr int LOD_TILE = 32;   // level-1 tile side
 constexpr int LOD_FUSED = 6;   // levels a block can finish: 32, 16, 8, 4, 2, 1
 
 struct LodArgs {
     const uint32_t* c0;
-    const float* v0;
+    const float* v0;  // level-0 velocity, or the maximum energy when FROM_MAXE
+    float* vel0;      // FROM_MAXE: level-0 velocity out (may alias v0)
+    float g2;         // FROM_MAXE: 2 g
     int w[LOD_FUSED + 1], h[LOD_FUSED + 1];  // level sizes 0 .. LOD_FUSED
     uint32_t* c[LOD_FUSED];                  // outputs of levels 1 .. LOD_FUSED
     float* v[LOD_FUSED];
@@ -118,6 +123,27 @@ struct LodArgs {
     bool vec2;                               // level-0 child pairs as uint2 / float2
 };
 
+template <bool FROM_MAXE>
+__device__ __forceinline__ float lod_vel0(const LodArgs& a, uint32_t i)
+{
+    const float x = __ldg(a.v0 + i);
+    if (!FROM_MAXE) return x;
+    const float v = __fsqrt_rn(__fmul_rn(a.g2, x));
+    a.vel0[i] = v;
+    return v;
+}
+
+template <bool FROM_MAXE>
+__device__ __forceinline__ float2 lod_vel0_pair(const LodArgs& a, uint32_t i)
+{
+    const float2 x = __ldg(reinterpret_cast<const float2*>(a.v0 + i));
+    if (!FROM_MAXE) return x;
+    const float2 v = make_float2(__fsqrt_rn(__fmul_rn(a.g2, x.x)), __fsqrt_rn(__fmul_rn(a.g2, x.y)));
+    *reinterpret_cast<float2*>(a.vel0 + i) = v;
+    return v;
+}
+
+template <bool FROM_MAXE>
 __global__ void __launch_bounds__(256) k_lod_fused(const __grid_constant__ LodArgs a)
 {
     __shared__ uint32_t sc[2][LOD_TILE][LOD_TILE + 1];
@@ -139,28 +165,28 @@ __global__ void __launch_bounds__(256) k_lod_fused(const __grid_constant__ LodAr
                 float m;
                 if (a.vec2) {  // w0 even: both columns exist and the pair is 8-byte aligned
                     const uint2 c_0 = __ldg(reinterpret_cast<const uint2*>(a.c0 + r0));
-                    const float2 v_0 = __ldg(reinterpret_cast<const float2*>(a.v0 + r0));
+                    const float2 v_0 = lod_vel0_pair<FROM_MAXE>(a, r0);
                     sum = (unsigned long long)c_0.x + c_0.y;
                     m = fmaxf(v_0.x, v_0.y);
                     if (hy) {
                         const uint2 c_1 = __ldg(reinterpret_cast<const uint2*>(a.c0 + r1));
-                        const float2 v_1 = __ldg(reinterpret_cast<const float2*>(a.v0 + r1));
+                        const float2 v_1 = lod_vel0_pair<FROM_MAXE>(a, r1);
                         sum += (unsigned long long)c_1.x + c_1.y;
                         m = fmaxf(m, fmaxf(v_1.x, v_1.y));
                     }
                 } else {
                     sum = __ldg(a.c0 + r0);
-                    m = __ldg(a.v0 + r0);
+                    m = lod_vel0<FROM_MAXE>(a, r0);
                     if (hx) {
                         sum += __ldg(a.c0 + r0 + 1);
-                        m = fmaxf(m, __ldg(a.v0 + r0 + 1));
+                        m = fmaxf(m, lod_vel0<FROM_MAXE>(a, r0 + 1));
                     }
                     if (hy) {
                         sum += __ldg(a.c0 + r1);
-                        m = fmaxf(m, __ldg(a.v0 + r1));
+                        m = fmaxf(m, lod_vel0<FROM_MAXE>(a, r1));
                         if (hx) {
                             sum += __ldg(a.c0 + r1 + 1);
-                            m = fmaxf(m, __ldg(a.v0 + r1 + 1));
+                            m = fmaxf(m, lod_vel0<FROM_MAXE>(a, r1 + 1));
                         }
                     }
                 }
@@ -225,51 +251,48 @@ extern "C" awo_status awo_finalize(const float* d_maxe, awo_grid g, float gravit
     return launch_status();
 }
 
-extern "C" awo_status awo_overlay_lod(const uint32_t* d_count, const float* d_vel, awo_grid g, int32_t levels,
-                                      uint32_t* const* d_count_lv, float* const* d_vel_lv, void* stream)
+// Levels 1 .. levels-1 from level 0 = (d_count, v0): one fused launch for
+// levels 1 .. LOD_FUSED, then one launch per further level.  from_maxe: v0
+// is the maximum energy and level 0's velocity is written to d_vel (g2 = 2 g).
+static awo_status lod_levels(const uint32_t* d_count, const float* v0, bool from_maxe, float g2, float* d_vel,
+                             awo_grid g, int32_t levels, uint32_t* const* d_count_lv, float* const* d_vel_lv,
+                             cudaStream_t s)
 {
-    if (!d_count || !d_vel || !grid_ok(g) || levels < 1 || levels > 16) return AWO_EINVAL;
-    if (levels > 1 && (!d_count_lv || !d_vel_lv)) return AWO_EINVAL;
-    for (int l = 0; l + 1 < levels; ++l)
-        if (!d_count_lv[l] || !d_vel_lv[l]) return AWO_EINVAL;
-    cudaStream_t s = as_stream(stream);
-    const uint32_t* ci = d_count;
-    const float* vi = d_vel;
-    int w = g.width, h = g.height;
-    int l = 1;
-    if (levels > 1) {  // levels 1 .. up to LOD_FUSED in one launch
-        LodArgs a;
-        memset(&a, 0, sizeof(a));
-        a.c0 = d_count;
-        a.v0 = d_vel;
-        a.n_out = levels - 1 < LOD_FUSED ? levels - 1 : LOD_FUSED;
-        a.w[0] = g.width;
-        a.h[0] = g.height;
-        for (int k = 1; k <= a.n_out; ++k) {
-            a.w[k] = (a.w[k - 1] + 1) / 2;
-            a.h[k] = (a.h[k - 1] + 1) / 2;
-            a.c[k - 1] = d_count_lv[k - 1];
-            a.v[k - 1] = d_vel_lv[k - 1];
-        }
-        a.vec2 = g.width % 2 == 0 && ((((uintptr_t)d_count) | ((uintptr_t)d_vel)) & 7u) == 0;
-        const dim3 grid((unsigned)((a.w[1] + LOD_TILE - 1) / LOD_TILE), (unsigned)((a.h[1] + LOD_TILE - 1) / LOD_TILE));
-        k_lod_fused<<<grid, 256, 0, s>>>(a);
-        awo_status st = launch_status();
-        if (st != AWO_OK) return st;
-        l = 1 + a.n_out;
-        ci = d_count_lv[a.n_out - 1];
-        vi = d_vel_lv[a.n_out - 1];
-        w = a.w[a.n_out];
-        h = a.h[a.n_out];
+    LodArgs a;
+    memset(&a, 0, sizeof(a));
+    a.c0 = d_count;
+    a.v0 = v0;
+    a.vel0 = d_vel;
+    a.g2 = g2;
+    a.n_out = levels - 1 < LOD_FUSED ? levels - 1 : LOD_FUSED;
+    a.w[0] = g.width;
+    a.h[0] = g.height;
+    for (int k = 1; k <= a.n_out; ++k) {
+        a.w[k] = (a.w[k - 1] + 1) / 2;
+        a.h[k] = (a.h[k - 1] + 1) / 2;
+        a.c[k - 1] = d_count_lv[k - 1];
+        a.v[k - 1] = d_vel_lv[k - 1];
     }
-    for (; l < levels; ++l) {
+    a.vec2 = g.width % 2 == 0 &&
+             ((((uintptr_t)d_count) | ((uintptr_t)v0) | (from_maxe ? (uintptr_t)d_vel : (uintptr_t)0)) & 7u) == 0;
+    const dim3 grid((unsigned)((a.w[1] + LOD_TILE - 1) / LOD_TILE), (unsigned)((a.h[1] + LOD_TILE - 1) / LOD_TILE));
+    if (from_maxe)
+        k_lod_fused<true><<<grid, 256, 0, s>>>(a);
+    else
+        k_lod_fused<false><<<grid, 256, 0, s>>>(a);
+    awo_status st = launch_status();
+    if (st != AWO_OK) return st;
+    const uint32_t* ci = d_count_lv[a.n_out - 1];
+    const float* vi = d_vel_lv[a.n_out - 1];
+    int w = a.w[a.n_out], h = a.h[a.n_out];
+    for (int l = 1 + a.n_out; l < levels; ++l) {
         int w2 = (w + 1) / 2, h2 = (h + 1) / 2;
         const bool vec = w % 4 == 0 && h % 2 == 0 && ((((uintptr_t)ci) | ((uintptr_t)vi)) & 15u) == 0 &&
                          ((((uintptr_t)d_count_lv[l - 1]) | ((uintptr_t)d_vel_lv[l - 1])) & 7u) == 0;
         const int64_t items = vec ? (int64_t)(w2 / 2) * h2 : (int64_t)w2 * h2;
         k_lod_level<<<stream_blocks(items, 256), 256, 0, s>>>(ci, vi, w, h, d_count_lv[l - 1], d_vel_lv[l - 1], w2,
                                                               h2, vec);
-        awo_status st = launch_status();
+        st = launch_status();
         if (st != AWO_OK) return st;
         ci = d_count_lv[l - 1];
         vi = d_vel_lv[l - 1];
@@ -277,4 +300,29 @@ extern "C" awo_status awo_overlay_lod(const uint32_t* d_count, const float* d_ve
         h = h2;
     }
     return AWO_OK;
+}
+
+extern "C" awo_status awo_overlay_lod(const uint32_t* d_count, const float* d_vel, awo_grid g, int32_t levels,
+                                      uint32_t* const* d_count_lv, float* const* d_vel_lv, void* stream)
+{
+    if (!d_count || !d_vel || !grid_ok(g) || levels < 1 || levels > 16) return AWO_EINVAL;
+    if (levels > 1 && (!d_count_lv || !d_vel_lv)) return AWO_EINVAL;
+    for (int l = 0; l + 1 < levels; ++l)
+        if (!d_count_lv[l] || !d_vel_lv[l]) return AWO_EINVAL;
+    if (levels == 1) return AWO_OK;
+    return lod_levels(d_count, d_vel, false, 0.0f, nullptr, g, levels, d_count_lv, d_vel_lv, as_stream(stream));
+}
+
+extern "C" awo_status awo_finalize_lod(const float* d_maxe, const uint32_t* d_count, awo_grid g, float gravity,
+                                       int32_t levels, float* d_vel, uint32_t* const* d_count_lv,
+                                       float* const* d_vel_lv, void* stream)
+{
+    if (!d_maxe || !d_count || !d_vel || !grid_ok(g) || levels < 1 || levels > 16) return AWO_EINVAL;
+    if (!(gravity > 0.0f) || !(gravity < 1.0e38f)) return AWO_EINVAL;
+    if (levels > 1 && (!d_count_lv || !d_vel_lv)) return AWO_EINVAL;
+    for (int l = 0; l + 1 < levels; ++l)
+        if (!d_count_lv[l] || !d_vel_lv[l]) return AWO_EINVAL;
+    if (levels == 1) return awo_finalize(d_maxe, g, gravity, d_vel, stream);
+    return lod_levels(d_count, d_maxe, true, 2.0f * gravity, d_vel, g, levels, d_count_lv, d_vel_lv,
+                      as_stream(stream));
 }

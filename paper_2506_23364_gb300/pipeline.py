@@ -12,7 +12,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import (AWO_OK, Grid, SimParams, awo_decode_u16, awo_finalize, awo_normals, awo_overlay_lod,
+from . import (AWO_OK, Grid, SimParams, awo_decode_u16, awo_finalize_lod, awo_normals,
                awo_release, awo_release_from_mask, awo_release_texture, awo_release_texture_dims,
                awo_release_texture_workspace_bytes, awo_release_workspace_bytes, awo_simulate,
                awo_simulate_workspace_bytes, grid, lod_shapes, stats_dict)
@@ -132,10 +132,9 @@ class Overlay:
 
     @_ranged("awo overlay")
     def overlay(self, gravity: float = 9.81, stream=None):
-        """c'-d: velocity indicator and mipmap."""
-        awo_finalize(self.maxe, self.g, gravity, self.vel, stream)
-        if self.levels > 1:
-            awo_overlay_lod(self.count, self.vel, self.g, self.levels, self.count_lv, self.vel_lv, stream)
+        """c'-d: velocity indicator and mipmap, in one pass."""
+        awo_finalize_lod(self.maxe, self.count, self.g, gravity, self.levels, self.vel, self.count_lv, self.vel_lv,
+                         stream)
 
     def run(self, slope_lo_deg: float, slope_hi_deg: float, params: SimParams, decode_scale: float = 0.1,
             stream=None):

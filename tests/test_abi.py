@@ -63,6 +63,7 @@ def test_bad_grids_rejected_on_host(L, g):
     fake = ctypes.c_void_p(16)  # never dereferenced: validation fails first
     assert L.awo_normals(fake, G, fake, fake, None, None) == awo.AWO_EINVAL
     assert L.awo_finalize(fake, G, ctypes.c_float(9.81), fake, None) == awo.AWO_EINVAL
+    assert L.awo_finalize_lod(fake, fake, G, ctypes.c_float(9.81), 1, fake, None, None, None) == awo.AWO_EINVAL
 
 
 def test_bad_arguments_rejected_on_host(L):
@@ -88,6 +89,12 @@ def test_bad_arguments_rejected_on_host(L):
     assert L.awo_overlay_lod(fake, fake, G, 0, arr, arr, None) == awo.AWO_EINVAL
     assert L.awo_overlay_lod(fake, fake, G, 17, arr, arr, None) == awo.AWO_EINVAL
     assert L.awo_overlay_lod(fake, fake, G, 2, None, None, None) == awo.AWO_EINVAL
+    g98 = ctypes.c_float(9.81)
+    assert L.awo_finalize_lod(fake, fake, G, g98, 0, fake, arr, arr, None) == awo.AWO_EINVAL
+    assert L.awo_finalize_lod(fake, fake, G, g98, 17, fake, arr, arr, None) == awo.AWO_EINVAL
+    assert L.awo_finalize_lod(fake, fake, G, g98, 2, fake, None, None, None) == awo.AWO_EINVAL
+    assert L.awo_finalize_lod(fake, None, G, g98, 2, fake, arr, arr, None) == awo.AWO_EINVAL
+    assert L.awo_finalize_lod(fake, fake, G, ctypes.c_float(0.0), 2, fake, arr, arr, None) == awo.AWO_EINVAL
 
 
 def test_batched_structs_and_host_validation(L):

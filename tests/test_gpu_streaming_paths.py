@@ -143,3 +143,32 @@ def test_snow_paths(shape, offset):
     ra, rrgba = oracle.snow_cover(h, rn[2], 1200.0, 400.0, 35.0, 6.0)
     assert np.array_equal(a.cpu().numpy(), ra)
     assert np.array_equal(rgba.cpu().numpy(), rrgba)
+
+
+@pytest.mark.parametrize("shape,levels", [((64, 128), 6), ((33, 257), 5), ((777, 1000), 11), ((1, 700), 11),
+                                          ((130, 2), 8), ((5, 3), 1)])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_finalize_lod_one_pass(shape, levels, offset):
+    """awo_finalize_lod equals the oracle's velocity and mipmap (and so
+    awo_finalize followed by awo_overlay_lod), also writing the velocity over
+    the maximum energy in place."""
+    H, W = shape
+    rng = np.random.default_rng(H * 7 + W + offset)
+    cnt = rng.integers(0, 1000, size=(H, W), dtype=np.uint64).astype(np.uint32)
+    cnt[rng.random((H, W)) < 0.1] = 0xFFFFFFF0
+    maxe = rng.uniform(0, 300, size=(H, W)).astype(np.float32)
+    maxe[rng.random((H, W)) < 0.3] = 0
+    g = awo.grid(W, H, 10.0)
+    vel = oracle.finalize(maxe, 9.81)
+    rc, rv = oracle.lod(cnt, vel, levels)
+    shapes = awo.lod_shapes(g, levels)
+    for in_place in (False, True):
+        dm = _dev(maxe, offset)
+        dv = dm if in_place else _empty((H, W), torch.float32, offset)
+        cl = [_empty(s, torch.int32, offset) for s in shapes[1:]]
+        vl = [_empty(s, torch.float32, offset) for s in shapes[1:]]
+        awo.awo_finalize_lod(dm, _dev(cnt.view(np.int32), offset), g, 9.81, levels, dv, cl, vl)
+        assert np.array_equal(dv.cpu().numpy(), vel)
+        for l in range(1, levels):
+            assert np.array_equal(cl[l - 1].cpu().numpy().view(np.uint32), rc[l]), l
+            assert np.array_equal(vl[l - 1].cpu().numpy(), rv[l]), l
