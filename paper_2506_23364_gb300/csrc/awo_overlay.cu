@@ -1,9 +1,12 @@
 // awo_overlay.cu -- velocity indicator and overlay mipmap (Sec. 3, Fig. 4).
 //
-// Both are streaming passes.  The mipmap is built level by level: each thread
-// reduces 2x2 blocks of the level above (two output texels from 16-byte rows
-// when the level allows it; counts summed in 64 bits and saturated,
-// velocities by max), so every level reads its parent once.
+// Both are streaming passes.  Levels 1-6 of the mipmap come from one kernel:
+// a block reduces its 64 x 64 tile of level 0 to level 1 and then, in shared
+// memory, to each further level (counts summed in 64 bits and saturated,
+// velocities by max), so level 0 is read once and every level written once;
+// deeper levels are built one launch per level from their parent.  The
+// workflow's call also makes the velocity from the maximum energy inside the
+// same pass (awo_finalize_lod).
 #include <string.h>
 
 #include "awo_internal.cuh"

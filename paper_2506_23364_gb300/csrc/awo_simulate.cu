@@ -32,6 +32,10 @@
 //    the L2 spends on the duplicate reductions.
 //  * Philox4x32-10 round keys are computed once on the host and read from the
 //    kernel's parameter bank.
+//  * On grids of at least 2^20 cells the 2x2 footprint of a move is one
+//    texture gather through a texture object that views the DEM's words
+//    (clamp addressing is the footprint clamp; indices and weights are still
+//    computed here), in place of four loads, their addresses and clamps.
 //  * Arithmetic is FP32 with explicit round-to-nearest intrinsics: no fused
 //    multiply-add, IEEE sqrt and reciprocal, so every particle follows the
 //    formulas of awo.h bit for bit.
