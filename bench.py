@@ -58,8 +58,8 @@ ALG_OPS_PER_VISIT = 126
 # L2 throughput of the same capture (lts__throughput.avg.pct_of_peak_sustained_elapsed
 # / 100): the particle kernel's share of the L2's own ceiling, keyed like the
 # traffic above.
-L2_THROUGHPUT_FRAC: dict[str, float] = {"51ddc06ae445bf39": 0.64541501}
-DRAM_BYTES_PER_VISIT: dict[str, float] = {"51ddc06ae445bf39": (275.738624e6 + 55.826432e6) / 1754008332}
+L2_THROUGHPUT_FRAC: dict[str, float] = {"843ee4cf528eda01": 0.64920426}
+DRAM_BYTES_PER_VISIT: dict[str, float] = {"843ee4cf528eda01": (276.226048e6 + 55.794176e6) / 1754008332}
 
 
 def _args():
