@@ -239,8 +239,9 @@ awo_status awo_release_noalloc(const float* d_tan2, awo_grid g, double slope_lo_
  * Gathers: on grids of at least 2^20 cells whose row pitch (4 * width bytes)
  * and d_h are aligned to the device's texture pitch alignment (32 bytes on
  * GB300), the particle kernel fetches each 2x2 footprint with one texture
- * gather through a texture object that views d_h (clamp addressing, which
- * is the i1, j1 clamp above; indices and weights computed as stated).  The
+ * gather through a texture object that views d_h's 32-bit words (returned
+ * bit for bit, subnormal heights included; clamp addressing, which is the
+ * i1, j1 clamp above; indices and weights computed as stated).  The
  * object is created at the first call with that (d_h, width, height, device)
  * and kept for the life of the process, so that a captured CUDA graph keeps
  * a valid one; after 256 such buffers, further ones use plain loads, and a
