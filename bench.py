@@ -324,10 +324,11 @@ def run_awo(args, R: Ranks):
     torch.cuda.synchronize()
     st = ov.stats_dict()
     visits = st["total_steps"] + st["n_traj"]
-    # decode, normals, release (mask, scan, scatter), particle prologue and kernel, then velocity and
-    # mipmap: one launch for both and levels 1..6, one per further level (velocity alone without a mipmap)
+    # decode and normals (one launch), release (mask, scan, scatter), particle prologue and kernel, then
+    # velocity and mipmap: one launch for both and levels 1..6, one per further level (velocity alone
+    # without a mipmap)
     lod_launches = 1 if w.lod_levels <= 1 else 1 + max(w.lod_levels - 1 - 6, 0)
-    launches_per_step = (1 if w.quantised else 0) + 1 + 3 + 2 + lod_launches
+    launches_per_step = 1 + 3 + 2 + lod_launches
 
     peaks_probe = _probe_peaks(torch, awo)
     clocks = ClockSampler(R.local)
@@ -723,6 +724,8 @@ def run_stages(args, R: Ranks):
         ("decode", lambda: awo.awo_decode_u16(ov.q, g, 0.1, ov.h), 6 * n),
         ("normals (+tan2)", lambda: awo.awo_normals(ov.h, g, ov.normal, ov.tan2, None), 20 * n),
         ("normals (+tan2, slope_deg)", lambda: awo.awo_normals(ov.h, g, ov.normal, ov.tan2, ov.slope), 24 * n),
+        ("decode + normals (one pass)", lambda: awo.awo_normals_u16(ov.q, g, 0.1, ov.h, ov.normal, ov.tan2, None),
+         22 * n),
         ("release (3 passes)", lambda: awo.awo_release(ov.tan2, g, w.slope_lo_deg, w.slope_hi_deg, ov.mask, ov.cells,
                                                        ov.n_rel, ov.ws_rel), 5 * n + 4 * n_rel),
         ("release texture 2x (3 passes)", rel_tex, 4 * n + wr * hr + 4 * n_rel_t),

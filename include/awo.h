@@ -116,6 +116,16 @@ awo_status awo_normals(const float* d_h, awo_grid g, float* d_normal, float* d_t
                        float* d_slope_deg, void* stream);
 
 /*
+ * a0 + a1 in one pass: exactly awo_decode_u16(d_q, g, scale, d_h) followed
+ * by awo_normals(d_h, g, d_normal, d_tan2, d_slope_deg), with the heights
+ * decoded where the normals read them, so d_h is written once and never read
+ * back.  With all three outputs null it is awo_decode_u16.  Arguments,
+ * ranges and errors as in the two calls.
+ */
+awo_status awo_normals_u16(const uint16_t* d_q, awo_grid g, float scale, float* d_h, float* d_normal,
+                           float* d_tan2, float* d_slope_deg, void* stream);
+
+/*
  * b. Release cells (Sec. 5.2: a texel is a potential release point when its
  * local steepness lies in the user's range; the node outputs a binary map).
  * Exact.  T = tan(deg * pi / 180)^2 is computed on the host in double and

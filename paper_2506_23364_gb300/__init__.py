@@ -135,6 +135,7 @@ def lib() -> ctypes.CDLL:
         "awo_simulate_workspace_bytes": (sz, [u32]),
         "awo_simulate": (st, [vp, Grid, vp, vp, u32, ctypes.POINTER(SimParams), vp, vp, vp, vp, sz, vp]),
         "awo_finalize": (st, [vp, Grid, f32, vp, vp]),
+        "awo_normals_u16": (st, [vp, Grid, f32, vp, vp, vp, vp, vp]),
         "awo_overlay_lod": (st, [vp, vp, Grid, i32, vp, vp, vp]),
         "awo_finalize_lod": (st, [vp, vp, Grid, f32, i32, vp, vp, vp, vp]),
         "awo_simulate_batched_workspace_bytes": (sz, [vp, i32]),
@@ -210,6 +211,17 @@ def awo_normals(h: torch.Tensor, g: Grid, normal=None, tan2=None, slope_deg=None
     _check(lib().awo_normals(_dev(h, torch.float32, n, "h"), g, _dev(normal, torch.float32, 3 * n, "normal"),
                              _dev(tan2, torch.float32, n, "tan2"), _dev(slope_deg, torch.float32, n, "slope_deg"),
                              _stream(stream)), "awo_normals")
+
+
+def awo_normals_u16(q: torch.Tensor, g: Grid, scale: float, h: torch.Tensor, normal=None, tan2=None, slope_deg=None,
+                    stream=None):
+    """awo_decode_u16 then awo_normals in one pass (see awo.h)."""
+    if q.dtype not in (torch.uint16, torch.int16):
+        raise TypeError("q must be uint16 (or int16 bits)")
+    n = g.cells
+    _check(lib().awo_normals_u16(_dev(q, q.dtype, n, "q"), g, scale, _dev(h, torch.float32, n, "h"),
+                                 _dev(normal, torch.float32, 3 * n, "normal"), _dev(tan2, torch.float32, n, "tan2"),
+                                 _dev(slope_deg, torch.float32, n, "slope_deg"), _stream(stream)), "awo_normals_u16")
 
 
 def awo_release_workspace_bytes(g: Grid) -> int:

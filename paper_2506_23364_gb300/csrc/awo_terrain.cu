@@ -85,9 +85,38 @@ __device__ __forceinline__ void normal_of(float gx, float gy, float& nx, float& 
 
 __device__ __forceinline__ float slope_deg_of(float t2) { return atanf(sqrtf(t2)) * 57.295779513082320876f; }
 
-__global__ void __launch_bounds__(256) k_normals(const float* __restrict__ h, int W, int H, float cs,
+// Heights for k_normals: FP32 metres, or (FROM_U16) uint16 words decoded
+// exactly as k_decode_u16 does, h = (float)q * scale.
+template <bool FROM_U16>
+struct HeightSrc {
+    const void* p;
+    float scale;
+    __device__ __forceinline__ float at(int64_t i) const
+    {
+        if (FROM_U16) return __fmul_rn(__uint2float_rn((unsigned)__ldg(static_cast<const uint16_t*>(p) + i)), scale);
+        return __ldg(static_cast<const float*>(p) + i);
+    }
+    // four consecutive heights from i (16-byte aligned floats / 8-byte aligned words)
+    __device__ __forceinline__ float4 at4(int64_t i) const
+    {
+        if (FROM_U16) {
+            const uint2 w = __ldg(reinterpret_cast<const uint2*>(static_cast<const uint16_t*>(p) + i));
+            return make_float4(__fmul_rn(__uint2float_rn(w.x & 0xffffu), scale),
+                               __fmul_rn(__uint2float_rn(w.x >> 16), scale),
+                               __fmul_rn(__uint2float_rn(w.y & 0xffffu), scale),
+                               __fmul_rn(__uint2float_rn(w.y >> 16), scale));
+        }
+        return __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(p) + i));
+    }
+};
+
+// FROM_U16: the heights are decoded from uint16 words and also written to
+// h_out (each thread writes the cells of its run), so a0 and a1 take one
+// pass: awo_decode_u16 followed by awo_normals, without re-reading h.
+template <bool FROM_U16>
+__global__ void __launch_bounds__(256) k_normals(const HeightSrc<FROM_U16> h, int W, int H, float cs,
                                                  float* __restrict__ nrm, float* __restrict__ tan2,
-                                                 float* __restrict__ slope_deg, bool vec4)
+                                                 float* __restrict__ slope_deg, float* __restrict__ h_out, bool vec4)
 {
     const int64_t plane = (int64_t)W * H;
     const uint32_t runs = (uint32_t)((W + 3) >> 2);
@@ -100,11 +129,12 @@ __global__ void __launch_bounds__(256) k_normals(const float* __restrict__ h, in
         const float deny = yr - yl == 2 ? den2 : den1;
         const int64_t row = (int64_t)y * W;
         if (vec4) {
-            const float4 c = __ldg(reinterpret_cast<const float4*>(h + row + x0));
-            const float4 up = __ldg(reinterpret_cast<const float4*>(h + (int64_t)yl * W + x0));
-            const float4 dn = __ldg(reinterpret_cast<const float4*>(h + (int64_t)yr * W + x0));
-            const float left = x0 > 0 ? __ldg(h + row + x0 - 1) : c.x;
-            const float right = x0 + 4 < W ? __ldg(h + row + x0 + 4) : c.w;
+            const float4 c = h.at4(row + x0);
+            const float4 up = h.at4((int64_t)yl * W + x0);
+            const float4 dn = h.at4((int64_t)yr * W + x0);
+            const float left = x0 > 0 ? h.at(row + x0 - 1) : c.x;
+            const float right = x0 + 4 < W ? h.at(row + x0 + 4) : c.w;
+            if (FROM_U16) *reinterpret_cast<float4*>(h_out + row + x0) = c;
             const float hc[6] = {left, c.x, c.y, c.z, c.w, right};
             const float hu[4] = {up.x, up.y, up.z, up.w}, hd[4] = {dn.x, dn.y, dn.z, dn.w};
             float o_nx[4], o_ny[4], o_nz[4], o_t2[4];
@@ -135,13 +165,12 @@ __global__ void __launch_bounds__(256) k_normals(const float* __restrict__ h, in
             for (int x = x0; x < x_end; ++x) {
                 const int xl = x > 0 ? x - 1 : 0, xr = x < W - 1 ? x + 1 : W - 1;
                 float gx = 0.0f, gy = 0.0f;
-                if (xr > xl) gx = __fdiv_rn(__fsub_rn(__ldg(h + row + xr), __ldg(h + row + xl)),
-                                           xr - xl == 2 ? den2 : den1);
-                if (yr > yl) gy = __fdiv_rn(__fsub_rn(__ldg(h + (int64_t)yr * W + x), __ldg(h + (int64_t)yl * W + x)),
-                                           deny);
+                if (xr > xl) gx = __fdiv_rn(__fsub_rn(h.at(row + xr), h.at(row + xl)), xr - xl == 2 ? den2 : den1);
+                if (yr > yl) gy = __fdiv_rn(__fsub_rn(h.at((int64_t)yr * W + x), h.at((int64_t)yl * W + x)), deny);
                 float nx, ny, nz, t2;
                 normal_of(gx, gy, nx, ny, nz, t2);
                 const int64_t i = row + x;
+                if (FROM_U16) h_out[i] = h.at(i);
                 if (nrm) {
                     nrm[i] = nx;
                     nrm[plane + i] = ny;
@@ -521,8 +550,22 @@ extern "C" awo_status awo_normals(const float* d_h, awo_grid g, float* d_normal,
     const int64_t items = (int64_t)((g.width + 3) / 4) * g.height;
     auto a16 = [](const void* p) { return p == nullptr || (((uintptr_t)p) & 15u) == 0; };
     const bool vec4 = (g.width % 4) == 0 && a16(d_h) && a16(d_normal) && a16(d_tan2) && a16(d_slope_deg);
-    k_normals<<<stream_blocks(items, 256), 256, 0, as_stream(stream)>>>(d_h, g.width, g.height, g.cell_size,
-                                                                         d_normal, d_tan2, d_slope_deg, vec4);
+    k_normals<false><<<stream_blocks(items, 256), 256, 0, as_stream(stream)>>>(
+        HeightSrc<false>{d_h, 1.0f}, g.width, g.height, g.cell_size, d_normal, d_tan2, d_slope_deg, nullptr, vec4);
+    return launch_status();
+}
+
+extern "C" awo_status awo_normals_u16(const uint16_t* d_q, awo_grid g, float scale, float* d_h, float* d_normal,
+                                      float* d_tan2, float* d_slope_deg, void* stream)
+{
+    if (!d_q || !d_h || !grid_ok(g) || !(scale > 0.0f) || !(scale < 3.0e38f)) return AWO_EINVAL;
+    if (!d_normal && !d_tan2 && !d_slope_deg) return awo_decode_u16(d_q, g, scale, d_h, stream);
+    const int64_t items = (int64_t)((g.width + 3) / 4) * g.height;
+    auto a16 = [](const void* p) { return p == nullptr || (((uintptr_t)p) & 15u) == 0; };
+    const bool vec4 = (g.width % 4) == 0 && (((uintptr_t)d_q) & 7u) == 0 && a16(d_h) && a16(d_normal) &&
+                      a16(d_tan2) && a16(d_slope_deg);
+    k_normals<true><<<stream_blocks(items, 256), 256, 0, as_stream(stream)>>>(
+        HeightSrc<true>{d_q, scale}, g.width, g.height, g.cell_size, d_normal, d_tan2, d_slope_deg, d_h, vec4);
     return launch_status();
 }
 

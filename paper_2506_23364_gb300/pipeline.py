@@ -12,7 +12,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import (AWO_OK, Grid, SimParams, awo_decode_u16, awo_finalize_lod, awo_normals,
+from . import (AWO_OK, Grid, SimParams, awo_finalize_lod, awo_normals, awo_normals_u16,
                awo_release, awo_release_from_mask, awo_release_texture, awo_release_texture_dims,
                awo_release_texture_workspace_bytes, awo_release_workspace_bytes, awo_simulate,
                awo_simulate_workspace_bytes, grid, lod_shapes, stats_dict)
@@ -97,9 +97,10 @@ class Overlay:
     @_ranged("awo terrain")
     def terrain(self, slope_lo_deg: float, slope_hi_deg: float, decode_scale: float = 0.1, stream=None):
         """a0-b: decode, normals and release (the count stays on the device)."""
-        if self.quantised:
-            awo_decode_u16(self.q, self.g, decode_scale, self.h, stream)
-        awo_normals(self.h, self.g, self.normal, self.tan2, self.slope, stream)
+        if self.quantised:  # decode and normals in one pass
+            awo_normals_u16(self.q, self.g, decode_scale, self.h, self.normal, self.tan2, self.slope, stream)
+        else:
+            awo_normals(self.h, self.g, self.normal, self.tan2, self.slope, stream)
         if self.release_log2:
             awo_release_texture(self.tan2, self.g, self.release_log2, slope_lo_deg, slope_hi_deg, self.mask,
                                 self.cells, self.n_rel, self.ws_rel, stream)
@@ -112,8 +113,9 @@ class Overlay:
         """a0-b': decode, normals and the release list from a caller's uint8
         mask (at the release texture's resolution)."""
         if self.quantised:
-            awo_decode_u16(self.q, self.g, decode_scale, self.h, stream)
-        awo_normals(self.h, self.g, self.normal, self.tan2, self.slope, stream)
+            awo_normals_u16(self.q, self.g, decode_scale, self.h, self.normal, self.tan2, self.slope, stream)
+        else:
+            awo_normals(self.h, self.g, self.normal, self.tan2, self.slope, stream)
         awo_release_from_mask(mask, self.g_rel, self.cells, self.n_rel, self.ws_rel, stream)
 
     @_ranged("awo simulate")

@@ -70,6 +70,9 @@ def test_bad_arguments_rejected_on_host(L):
     G = awo.grid(16, 16, 10.0)
     fake = ctypes.c_void_p(256)
     assert L.awo_normals(None, G, fake, None, None, None) == awo.AWO_EINVAL
+    assert L.awo_normals_u16(None, G, ctypes.c_float(0.1), fake, fake, None, None, None) == awo.AWO_EINVAL
+    assert L.awo_normals_u16(fake, G, ctypes.c_float(0.1), None, fake, None, None, None) == awo.AWO_EINVAL
+    assert L.awo_normals_u16(fake, G, ctypes.c_float(0.0), fake, fake, None, None, None) == awo.AWO_EINVAL
     ws = awo.awo_release_workspace_bytes(G)
     assert L.awo_release(fake, G, 40.0, 30.0, fake, fake, fake, fake, ws, None) == awo.AWO_EINVAL
     assert L.awo_release(fake, G, 30.0, 90.0, fake, fake, fake, fake, ws, None) == awo.AWO_EINVAL

@@ -172,3 +172,32 @@ def test_finalize_lod_one_pass(shape, levels, offset):
         for l in range(1, levels):
             assert np.array_equal(cl[l - 1].cpu().numpy().view(np.uint32), rc[l]), l
             assert np.array_equal(vl[l - 1].cpu().numpy(), rv[l]), l
+
+
+@pytest.mark.parametrize("shape", SHAPES + [(2, 4), (3, 8)])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_normals_u16_one_pass(shape, offset):
+    """awo_normals_u16 writes the decoded heights and the normals of
+    awo_decode_u16 followed by awo_normals, on both paths."""
+    H, W = shape
+    rng = np.random.default_rng(H * 5 + W + offset)
+    q = rng.integers(0, 30000, size=shape, dtype=np.uint16)
+    g = awo.grid(W, H, 12.5)
+    h = oracle.decode_u16(q, 0.1)
+    rn, rt, rs = oracle.normals(h, 12.5)
+    dh = _empty((H, W), torch.float32, offset)
+    nrm = _empty((3, H, W), torch.float32, offset)
+    t2 = _empty((H, W), torch.float32, offset)
+    sd = _empty((H, W), torch.float32, offset)
+    awo.awo_normals_u16(_dev(q.view(np.int16), offset), g, 0.1, dh, nrm, t2, sd)
+    assert np.array_equal(dh.cpu().numpy(), h)
+    assert np.array_equal(nrm.cpu().numpy(), rn)
+    assert np.array_equal(t2.cpu().numpy(), rt)
+    assert np.allclose(sd.cpu().numpy(), rs, rtol=1e-6, atol=1e-5)
+    # tan2 only, and no output (decode alone)
+    dh2, t2b = _empty((H, W), torch.float32, offset), _empty((H, W), torch.float32, offset)
+    awo.awo_normals_u16(_dev(q.view(np.int16), offset), g, 0.1, dh2, None, t2b, None)
+    assert np.array_equal(dh2.cpu().numpy(), h) and np.array_equal(t2b.cpu().numpy(), rt)
+    dh3 = _empty((H, W), torch.float32, offset)
+    awo.awo_normals_u16(_dev(q.view(np.int16), offset), g, 0.1, dh3, None, None, None)
+    assert np.array_equal(dh3.cpu().numpy(), h)
