@@ -77,6 +77,8 @@ def _args():
     ap.add_argument("--e2e-instances", type=int, default=3, help="workflow instances of the pipelined end-to-end run")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extensions", action="store_true",
+                    help="skip the batched, served, differentiable and parabola runs of the default line")
     ap.add_argument("--cpu-threads", type=int, default=0, help="host threads of the oracle (0 = all cores)")
     ap.add_argument("--release-log2", type=int, default=0,
                     help="evaluate release points on a texture at 2^r x the DEM resolution (large/mid/tiny)")
@@ -402,8 +404,44 @@ def run_awo(args, R: Ranks):
             "clocks": clk, "kernel_sha": sha}
     if R.rank == 0 and R.world == 1 and not args.no_cpu_baseline and not args.release_log2:
         line["cpu_baseline"] = _cpu_baseline(w, args.cpu_seconds, args.cpu_threads or None)
+    if (R.world == 1 and args.workload == "large" and not args.crop and not args.release_log2
+            and not args.no_extensions):
+        line["extensions"] = _extensions(args, R)
     if R.rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def _extensions(args, R: Ranks) -> dict:
+    """Compact runs of the batched, served, differentiable and parabola
+    workloads (each function's own measurement, fewer steps), reported
+    beside the headline so that they are measured in the same run."""
+    import torch
+
+    keep = {"batched": ("value", "unit", "ms_per_step", "speedup_vs_plain", "rasters_equal_plain", "clocks"),
+            "served": ("value", "unit", "latency_ms", "ok", "mean_batch", "wall_s", "clocks"),
+            "differentiable": ("forward_ms", "backward_ms", "particles", "moves", "fd_rel_err"),
+            "parabola": ("value", "unit", "min_ms", "particles", "moves")}
+    out = {}
+    for name, fn, steps in (("batched", run_batched, 3), ("served", run_served, args.steps),
+                            ("differentiable", run_diff, 3), ("parabola", run_parabola, 10)):
+        a = argparse.Namespace(**vars(args))
+        a.steps, a.warmup = steps, 1
+        t0 = time.perf_counter()
+        try:
+            r = fn(a, R, emit=False)
+        except Exception as e:  # reported, not hidden: the headline line still prints
+            out[name] = {"error": repr(e)[:400]}
+            continue
+        d = {k: r[k] for k in keep[name] if k in r}
+        d["config"] = r.get("config", {}).get("workload")
+        if name == "batched":
+            d["plain_value"] = r["plain"]["value"]
+            d["regions_by_texture_gather"] = r["config"].get("regions_by_texture_gather")
+        d["wall_s"] = d.get("wall_s") or (time.perf_counter() - t0)
+        out[name] = d
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return out
 
 
 def _e2e(args, R, awo, w, ov, host_dem, run, steps_one, steps_all) -> dict:
@@ -484,7 +522,7 @@ def _region_params(awo, r):
     return awo.SimParams.make(**r.params)
 
 
-def run_batched(args, R: Ranks):
+def run_batched(args, R: Ranks, emit: bool = True) -> dict:
     """Many regions: each region run alone in sequence (the plain form) against
     one batched launch per pass (tuned once, replayed from a CUDA graph)."""
     import torch
@@ -520,8 +558,6 @@ def run_batched(args, R: Ranks):
 
     ms_plain = timed(plain, args.steps)
     steps_plain = sum(ov.stats_dict()["total_steps"] for ov in ovs)
-    del ovs
-    torch.cuda.empty_cache()
     batch = awo.Batch([r.dem_u16 for r in reqs], cs, params, [r.release_deg for r in reqs], quantised=True,
                       device=R.device)
     tuning, tune_ms = batch.tune()
@@ -533,21 +569,30 @@ def run_batched(args, R: Ranks):
     st = batch.stats_list()
     steps_batch = sum(x["total_steps"] for x in st)
     assert steps_batch == steps_plain, "batched and plain runs must make the same moves"
+    # every region's rasters and statistics from the graph replay against its plain run, on the device
+    same = all(torch.equal(bo.count, po.count) and torch.equal(bo.maxe, po.maxe) and torch.equal(bo.vel, po.vel)
+               and x == po.stats_dict() for bo, po, x in zip(batch.ovs, ovs, st))
+    assert same, "batched rasters differ from the plain runs"
+    paths = [awo.awo_dem_gather_path(ov.h, ov.g) for ov in batch.ovs]
+    del ovs
     cells = sum(r.dem_u16.size for r in reqs)
     line = {"metric": "aggregate trajectory-steps/s, batched regions", "value": steps_batch / (ms_batch / 1e3),
             "unit": UNIT, "n_gpus": R.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic (seeded fBm regions, uint16 dm)",
             "config": {"workload": f"batched-{len(reqs)}-regions-512..4096", "cells": cells,
                        "particles": sum(x["n_traj"] for x in st), "form": "one batched launch per pass, CUDA graph",
-                       "tuning": tuning.as_dict(), "tune_best_ms": tune_ms},
+                       "tuning": tuning.as_dict(), "tune_best_ms": tune_ms,
+                       "regions_by_texture_gather": paths.count("texture")},
+            "rasters_equal_plain": same,
             "plain": {"value": steps_plain / (ms_plain / 1e3), "ms_per_pass": ms_plain,
                       "form": "each region alone, in sequence, same stream"},
             "speedup_vs_plain": ms_plain / ms_batch, "clocks": clk}
-    if R.rank == 0:
+    if emit and R.rank == 0:
         print(json.dumps(line), flush=True)
+    return line
 
 
-def run_served(args, R: Ranks):
+def run_served(args, R: Ranks, emit: bool = True) -> dict:
     """Poisson arrivals of the batched workload's regions into the serving loop."""
     import torch
 
@@ -583,11 +628,12 @@ def run_served(args, R: Ranks):
                        "slots": 4, "max_batch": 16, "budget_gib": 96},
             "latency_ms": lat, "ok": len(ok), "mean_batch": float(np.mean([x.batch_size for x in ok])),
             "wall_s": t_end - t0, "peak_budget_gib": srv.sched.peak_in_use / 2 ** 30, "clocks": clk}
-    if R.rank == 0:
+    if emit and R.rank == 0:
         print(json.dumps(line), flush=True)
+    return line
 
 
-def run_diff(args, R: Ranks):
+def run_diff(args, R: Ranks, emit: bool = True) -> dict:
     """Differentiable workload: soft deposits on a 1024^2 fBm DEM, target at
     hidden friction parameters, L2 loss; forward and adjoint timed with CUDA
     events; the gradient checked against central differences (h = 1e-3)."""
@@ -632,11 +678,12 @@ def run_diff(args, R: Ranks):
             "grad_log_mu": g[0], "grad_log_k": g[1], "fd_log_mu": fd[0], "fd_log_k": fd[1],
             "fd_rel_err": [abs(g[0] - fd[0]) / abs(fd[0]), abs(g[1] - fd[1]) / abs(fd[1])],
             "grad_w_norm": float(gw.norm())}
-    if R.rank == 0:
+    if emit and R.rank == 0:
         print(json.dumps(line), flush=True)
+    return line
 
 
-def run_parabola(args, R: Ranks):
+def run_parabola(args, R: Ranks, emit: bool = True) -> dict:
     """Parabola-shaped stand-in (501 x 151, three given release cells, 2048
     particles each): the whole workflow per step, from the device-resident DEM
     and release mask."""
@@ -676,8 +723,9 @@ def run_parabola(args, R: Ranks):
             "vs_baseline": None, "context": "paper Table 1: weBIGeo 13.5 ms on an RTX 3070 (WebGPU) for its "
                                              "parabola dataset; different geometry and hardware",
             "particles": st["n_traj"], "moves": st["total_steps"], "min_ms": min(ts)}
-    if R.rank == 0:
+    if emit and R.rank == 0:
         print(json.dumps(line), flush=True)
+    return line
 
 
 def run_stages(args, R: Ranks):
@@ -809,6 +857,10 @@ def run_reference(args, R: Ranks):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded fBm + carved valleys, uint16 dm)",
             "config": dict(w.describe(), parallelism="host cores"),
+            "timed": (f"particle stage only (the oracle's trajectories), per step a uniform random sample of "
+                      f"{k} of {cells.size} release cells ({k / cells.size:.3g} of them); the GPU arm times the "
+                      f"whole workflow over every release cell"),
+            "reference_sample_frac": k / cells.size,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"per step {k} of {cells.size} release cells, all {w.traj_per_cell} "
                                        f"particles each (uniform random, seed 777)"},

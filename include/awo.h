@@ -267,6 +267,19 @@ awo_status awo_simulate(const float* d_h, awo_grid g, const uint32_t* d_cells,
                         awo_sim_stats* d_stats, void* d_ws, size_t ws_bytes, void* stream);
 
 /*
+ * Footprint path of a DEM buffer (a diagnostic of this library; the paper has
+ * no counterpart).  Sets *texture to 1 when the particle kernels
+ * (awo_simulate, awo_simulate_batched, the soft-deposit calls) fetch the 2x2
+ * footprints of the W x H DEM at d_h by one texture gather through a texture
+ * view of the buffer, 0 when they fetch them with four loads (grids under
+ * 2^20 cells, a base address or row pitch off the texture alignment, 256
+ * views already made, or `stream` being captured).  Like the first launch
+ * with that buffer, the call creates the view when one can be made.  Results
+ * never depend on the path.  AWO_EINVAL: d_h or texture NULL, or a bad grid.
+ */
+awo_status awo_dem_gather_path(const float* d_h, awo_grid g, void* stream, int32_t* texture);
+
+/*
  * c (batched). Particle trajectories for many regions in one persistent
  * launch (the paper's workflow re-run for many regions and parameter sets;
  * Sec. 5.2 lets the user change the parameters interactively).  Every request

@@ -133,6 +133,7 @@ def lib() -> ctypes.CDLL:
         "awo_release_texture_workspace_bytes": (sz, [Grid, i32]),
         "awo_release_texture": (st, [vp, Grid, i32, f64, f64, vp, vp, vp, vp, sz, vp]),
         "awo_simulate_workspace_bytes": (sz, [u32]),
+        "awo_dem_gather_path": (st, [vp, Grid, vp, ctypes.POINTER(i32)]),
         "awo_simulate": (st, [vp, Grid, vp, vp, u32, ctypes.POINTER(SimParams), vp, vp, vp, vp, sz, vp]),
         "awo_finalize": (st, [vp, Grid, f32, vp, vp]),
         "awo_normals_u16": (st, [vp, Grid, f32, vp, vp, vp, vp, vp]),
@@ -300,6 +301,14 @@ def awo_release_noalloc(tan2: torch.Tensor, g: Grid, slope_lo_deg: float, slope_
     _check(lib().awo_release_noalloc(_dev(tan2, torch.float32, c, "tan2"), g, slope_lo_deg, slope_hi_deg,
                                      _dev(mask, torch.uint8, c, "mask"), _dev(cells, cells.dtype, c, "cells"),
                                      _dev(n, n.dtype, 1, "n"), _stream(stream)), "awo_release_noalloc")
+
+
+def awo_dem_gather_path(h: torch.Tensor, g: Grid, stream=None) -> str:
+    """'texture' or 'loads': how the particle kernels fetch this DEM buffer's footprints."""
+    t = ctypes.c_int32(0)
+    _check(lib().awo_dem_gather_path(_dev(h, torch.float32, g.cells, "h"), g, _stream(stream), ctypes.byref(t)),
+           "awo_dem_gather_path")
+    return "texture" if t.value else "loads"
 
 
 def awo_simulate_workspace_bytes(n_cells_max: int) -> int:

@@ -301,6 +301,13 @@ using namespace awo;
 
 static size_t starts_offset() { return 256; }
 
+extern "C" awo_status awo_dem_gather_path(const float* d_h, awo_grid g, void* stream, int32_t* texture)
+{
+    if (!d_h || !texture || !grid_ok(g)) return AWO_EINVAL;
+    *texture = dem_texture(d_h, g, as_stream(stream)) != 0 ? 1 : 0;
+    return AWO_OK;
+}
+
 extern "C" size_t awo_simulate_workspace_bytes(uint32_t n_cells_max)
 {
     return starts_offset() + (size_t)n_cells_max * sizeof(TexelStart);

@@ -531,7 +531,7 @@ extern "C" const char* awo_status_string(awo_status s)
     return "unknown status";
 }
 
-extern "C" int32_t awo_version(void) { return 10200; }
+extern "C" int32_t awo_version(void) { return 10300; }
 
 extern "C" awo_status awo_decode_u16(const uint16_t* d_q, awo_grid g, float scale, float* d_h, void* stream)
 {

@@ -31,6 +31,7 @@ def test_reference_arm_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 2 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["timed"].startswith("particle stage only") and 0 < d["reference_sample_frac"] <= 1
 
 
 @pytest.mark.gpu

@@ -83,3 +83,29 @@ def test_bad_request_fails_alone_on_gpu():
     reqs[1].params = dict(reqs[1].params, persistence=2.0)
     srv, res = _serve(reqs, budget_bytes=8 << 30, n_slots=2, max_batch=4)
     assert [r.status for r in res] == ["ok", "error", "ok", "ok"]
+
+
+def test_same_result_alone_and_in_the_mix_with_texture_gather_regions():
+    """Regions of 2^20 cells and more (footprints by texture gather, as in the
+    served 512^2-4096^2 workload) share micro-batches with small ones (loads)
+    and still give their single-request overlays bit for bit."""
+    reqs = _requests(6)
+    rng = np.random.default_rng(11)
+    for k, (H, W) in enumerate([(1024, 1024), (1056, 1024)]):
+        z = inputs.fbm(max(H, W), 0.8, seed=600 + k, relief=2000.0)[:H, :W]
+        params = dict(mu=MU25 * float(np.exp(rng.uniform(np.log(0.5), np.log(1.5)))),
+                      drag_k=1e-3 * float(np.exp(rng.uniform(np.log(0.5), np.log(1.5)))),
+                      traj_per_cell=8 + 8 * k, max_steps=2000, seed=100 + k)
+        reqs.insert(2 + 3 * k, OverlayRequest(inputs.quantise_dm(z), 10.0, (35.0, 45.0), params, levels=2))
+    alone = [_alone(r) for r in reqs]
+    probe = awo.Overlay(1024, 1024, 10.0, quantised=True, levels=1)
+    assert awo.awo_dem_gather_path(probe.h, probe.g) == "texture"
+    srv, res = _serve(reqs, budget_bytes=8 << 30, n_slots=2, max_batch=4)
+    assert all(r.status == "ok" for r in res), [r.error for r in res]
+    for a, r in zip(alone, res):
+        for l in range(len(r.count_lv)):
+            assert np.array_equal(r.count_lv[l], a["count_lv"][l]), (r.id, l)
+            assert np.array_equal(r.vel_lv[l], a["vel_lv"][l]), (r.id, l)
+        assert r.stats == a["stats"]
+    big = [r for r, q in zip(res, reqs) if q.dem.size >= (1 << 20)]
+    assert len(big) == 2 and all(r.stats["n_traj"] > 0 for r in big)

@@ -83,3 +83,19 @@ def test_autograd_function(problem):
     gt, gw = prob.backward_raw(MU0, K0, wt, 2.0 * (D.detach() - Dstar))
     assert torch.allclose(torch.stack([log_mu.grad, log_k.grad]), gt.cpu(), rtol=1e-12, atol=0)
     assert torch.equal(wr.grad, gw)
+
+
+# ----------------------------------------------------------------------------
+# The differentiable workload's own shape: 1024^2 fBm DEM (uint16 dm), release
+# range of the 2048^2 workload, 128 particles per release cell, cap 2048,
+# release weights U(0.5, 1.5), target at hidden parameters (1.2 mu0, 0.8 k0).
+# ----------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def problem1024():
+    n = 1024
+    dem = inputs.quantise_dm(inputs.fbm(n, 0.8, seed=3, relief=3000.0 * (n / 2048.0) ** 0.8))
+    prob = awo.SoftOverlay(dem, 10.0, inputs.MID_RELEASE_DEG, traj_per_cell=128, max_steps=2048, seed=0)
+    cells = prob.cells[: prob.n_cells].cpu().numpy().view(np.uint32)
+    w = np.random.default_rng(3).uniform(0.5, 1.5, cells.size).astype(np.float32)
+    op = lambda mu, k: oracle.SimParams(mu=mu, drag_k=k, traj_per_cell=128, max_steps=2048, seed=0)
+    return oracle.decode_u16(dem), prob, cells, w, op
