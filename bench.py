@@ -51,15 +51,22 @@ ALG_BYTES_PER_VISIT = 24
 # domain test 8; energy and stop test 6; visited cell 5; floors 4.
 ALG_OPS_PER_VISIT = 126
 
-# DRAM bytes per visit of the particle kernel from an ncu capture (dram__bytes
-# read + write of a 6144^2 crop launch, divided by its visits), keyed by the
-# SHA-256 prefix of the kernel's code (comments removed) it was taken on; a
-# changed kernel reports traffic null until it is captured again.
-# L2 throughput of the same capture (lts__throughput.avg.pct_of_peak_sustained_elapsed
-# / 100): the particle kernel's share of the L2's own ceiling, keyed like the
-# traffic above.
-L2_THROUGHPUT_FRAC: dict[str, float] = {"843ee4cf528eda01": 0.64920426}
-DRAM_BYTES_PER_VISIT: dict[str, float] = {"843ee4cf528eda01": (276.226048e6 + 55.794176e6) / 1754008332}
+# Counters of the particle kernel from one ncu capture of a 6144^2 crop launch
+# of the 8192^2 workload (bench.py --workload large --crop 6144), per visit
+# (release visit or move attempt) of that launch, keyed by the SHA-256 prefix
+# of the kernel's code (comments removed) they were taken on; a changed kernel
+# reports them as null until it is captured again:
+#   dram: dram__bytes_read.sum + dram__bytes_write.sum
+#   lts_frac: lts__throughput.avg.pct_of_peak_sustained_elapsed / 100, the L2's
+#     own utilisation against its peak -- the L2 gather/reduction roofline
+#     fraction of the kernel
+#   red_sectors, read_sectors: lts__t_sectors_op_red.sum and
+#     lts__t_sectors_op_read.sum (the visits' reductions and the footprint
+#     reads that miss in L1/texture cache)
+KERNEL_COUNTERS: dict[str, dict[str, float]] = {
+    "843ee4cf528eda01": {"dram": (276.226048e6 + 55.794176e6) / 1754008332, "lts_frac": 0.64920426,
+                         "red_sectors": 3323214484 / 1754008332, "read_sectors": 19568102 / 1754008332},
+}
 
 
 def _args():
@@ -362,7 +369,8 @@ def run_awo(args, R: Ranks):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     sim_s = sim_ms / 1e3
     sha = _kernel_sha()
-    traffic = DRAM_BYTES_PER_VISIT.get(sha)
+    kc = KERNEL_COUNTERS.get(sha, {})
+    traffic = kc.get("dram")
     # issue / ALU ceiling: 152 SMs x 128 lanes x SM clock (max clock of the run)
     sms = torch.cuda.get_device_properties(R.device).multi_processor_count
     mhz = clk.get("sm_max_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
@@ -377,15 +385,16 @@ def run_awo(args, R: Ranks):
     roofline_hbm = {"achieved": alg_bytes / sim_s / 1e9, "peak": hbm, "unit": "GB/s",
                     "frac": alg_bytes / sim_s / 1e9 / hbm, "alg_bytes_per_launch": alg_bytes,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
-    l2 = {"gather_loads_per_s": 4 * visits / sim_s, "red_per_s": 2 * visits / sim_s,
-          "probe_l2_gather_loads_per_s": peaks_probe["l2_gather_per_s"],
-          "probe_l2_red_per_s": peaks_probe["l2_red_per_s"]}
-    l2["gather_frac"] = l2["gather_loads_per_s"] / l2["probe_l2_gather_loads_per_s"]
-    l2["red_frac"] = l2["red_per_s"] / l2["probe_l2_red_per_s"]
-    l2["frac_of_binding"] = max(l2["gather_frac"], l2["red_frac"])
-    # the per-lane probes scatter every lane; the kernel's lanes share sectors,
-    # so its rates exceed them: the ncu L2 throughput is the tighter figure
-    l2["ncu_lts_throughput_frac"] = L2_THROUGHPUT_FRAC.get(sha)
+    # L2: the hardware's own utilisation of the L2 for this kernel (ncu), the
+    # gather/reduction roofline fraction; sector rates beside it
+    l2 = {"frac": kc.get("lts_frac"), "source": "ncu lts__throughput.avg.pct_of_peak_sustained_elapsed, "
+                                                "6144^2 crop launch of the same kernel code",
+          "red_sector_ops_per_s": kc["red_sectors"] * visits / sim_s if kc else None,
+          "read_sectors_per_s": kc["read_sectors"] * visits / sim_s if kc else None,
+          "random_access_probe": {"l2_red_per_s": peaks_probe["l2_red_per_s"],
+                                  "l2_load_per_s": peaks_probe["l2_gather_per_s"],
+                                  "note": "per-lane hashed 4-byte accesses (one sector each); context, not a "
+                                          "ceiling: the kernel's lanes share sectors"}}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": R.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True, "scaling": "weak",

@@ -284,8 +284,10 @@ def soft_forward(h: np.ndarray, cs: float, cells: np.ndarray, weights: np.ndarra
 
 
 def soft_gradient(h: np.ndarray, cs: float, cells: np.ndarray, weights: np.ndarray, params: SimParams,
-                  G: np.ndarray, tau: float = SOFT_TAU, precision: str = "f32", threads: int = 1):
-    """FP64 reverse-mode gradient of sum(G * D): (d/dlog mu, d/dlog k), d/dw per release entry."""
+                  G: np.ndarray, tau: float = SOFT_TAU, precision: str = "f32", threads: int = 1,
+                  with_abs: bool = False):
+    """FP64 reverse-mode gradient of sum(G * D): (d/dlog mu, d/dlog k), d/dw per release entry;
+    with_abs: also the sums over particles of |each particle's (d/dlog mu, d/dlog k) term|."""
     from concurrent.futures import ThreadPoolExecutor
 
     creal, npr = _real(precision)
@@ -301,21 +303,24 @@ def soft_gradient(h: np.ndarray, cs: float, cells: np.ndarray, weights: np.ndarr
         c = np.ascontiguousarray(cells[ix])
         w = np.ascontiguousarray(weights[ix])
         gt = np.zeros(2, np.float64)
+        ga = np.zeros(2, np.float64)
         gw = np.zeros(c.size, np.float64)
         rc = lib(precision).orc_soft_gradient(_ptr(h), ctypes.c_int32(W), ctypes.c_int32(H), creal(cs), _ptr(c),
                                               ctypes.c_uint32(c.size), _ptr(w), ctypes.byref(p),
-                                              ctypes.c_double(tau), _ptr(G), _ptr(gt), _ptr(gw))
+                                              ctypes.c_double(tau), _ptr(G), _ptr(gt), _ptr(gw), _ptr(ga))
         _check(rc, "orc_soft_gradient")
-        return ix, gt, gw
+        return ix, gt, gw, ga
 
     with ThreadPoolExecutor(len(idx)) as ex:
         out = list(ex.map(one, idx))
     gtheta = np.zeros(2, np.float64)
+    gabs = np.zeros(2, np.float64)
     gw = np.zeros(cells.size, np.float64)
-    for ix, gt, g in out:
+    for ix, gt, g, ga in out:
         gtheta += gt
+        gabs += ga
         gw[ix] = g
-    return gtheta, gw
+    return (gtheta, gw, gabs) if with_abs else (gtheta, gw)
 
 
 def finalize(maxe: np.ndarray, gravity: float = 9.81, precision: str = "f32") -> np.ndarray:

@@ -670,7 +670,7 @@ int orc_soft_forward(const real* h, int32_t W, int32_t H, real cs, const uint32_
  * over the stored path (the path itself does not depend on mu, k, w). */
 int orc_soft_gradient(const real* h, int32_t W, int32_t H, real cs, const uint32_t* cells, uint32_t n_cells,
                       const double* weight, const orc_params* p, double tau, const double* G,
-                      double* grad_theta, double* grad_weight)
+                      double* grad_theta, double* grad_weight, double* grad_theta_abs)
 {
     int rc = check_params(W, H, cs, p);
     if (rc) return rc;
@@ -712,6 +712,10 @@ int orc_soft_gradient(const real* h, int32_t W, int32_t H, real cs, const uint32
             }
             grad_theta[0] += (double)p->mu * dmu;   /* d/dlog(mu) = mu d/dmu */
             grad_theta[1] += (double)p->drag_k * dk;
+            if (grad_theta_abs) { /* sum of |per-particle terms|: the conditioning of the sum over particles */
+                grad_theta_abs[0] += fabs((double)p->mu * dmu);
+                grad_theta_abs[1] += fabs((double)p->drag_k * dk);
+            }
         }
     }
     free(abar);

@@ -156,7 +156,9 @@ __global__ void __launch_bounds__(AWO_BATCH_MAX) k_batch_prepare(const __grid_co
         a.hdr->n_cells[t] = nc;
     }
     s_nc[t] = nc;
-    s_np[t] = t < (int)a.n_req ? (unsigned long long)nc * a.r[t].N : 0ull;
+    // particles for the particle kernel: none for a request with max_steps = 0
+    // (every particle capped at its release visit, counted by k_batch_starts)
+    s_np[t] = (t < (int)a.n_req && a.r[t].max_steps != 0u) ? (unsigned long long)nc * a.r[t].N : 0ull;
     for (int i = t; i < (int)a.n_req * 6; i += blockDim.x) (&a.hdr->stats[0][0])[i] = 0ull;
     __syncthreads();
     if (t == 0) {
@@ -190,14 +192,25 @@ __global__ void __launch_bounds__(256) k_batch_starts(const __grid_constant__ Ba
         const BatchReq& q = a.r[r];
         const uint32_t ci = g - s_cp[r];
         const uint32_t entry = __ldg(q.cells + ci);
+        bool ok;
         if (q.texel) {
             const TexelStart st = texel_start(q.h, q.W, q.H, q.tg, entry);
-            if (st.t != ~0u) atomicAdd(q.count + st.vcell, q.N);
+            ok = st.t != ~0u;
+            if (ok) atomicAdd(q.count + st.vcell, q.N);
             a.starts[q.starts_off + ci] = st;
         } else {
             const CellStart st = cell_start(q.h, q.W, q.H, q.n_grid, entry);
-            if (st.xy != ~0u) atomicAdd(q.count + entry, q.N);
+            ok = st.xy != ~0u;
+            if (ok) atomicAdd(q.count + entry, q.N);
             *reinterpret_cast<CellStart*>(a.starts + q.starts_off + ci) = st;
+        }
+        // particles of entries outside the grid are rejected; with max_steps = 0
+        // every particle is capped at its release visit (no particle kernel work)
+        unsigned long long* st6 = a.hdr->stats[r];
+        if (!ok) atomicAdd(st6 + 5, (unsigned long long)q.N);
+        if (ok && q.max_steps == 0u) {
+            atomicAdd(st6 + 1, (unsigned long long)q.N);
+            atomicAdd(st6 + 3, (unsigned long long)q.N);
         }
     }
 }
@@ -256,7 +269,10 @@ __global__ void __launch_bounds__(THREADS) k_batch_simulate(const __grid_constan
             if (p_r != cr) {
                 // all lanes are idle here; their positions are reset so that
                 // the loads of dead lanes stay inside the new request's grid
-                if (cr >= 0) AWO_FLUSH_COUNTERS(a.hdr->stats[cr]);
+                if (cr >= 0) {
+                    AWO_FOLD_LANE(true, q.max_steps);
+                    AWO_FLUSH_COUNTERS(a.hdr->stats[cr]);
+                }
                 cr = p_r;
                 q = load_req(a, cr);
                 u = v = 0.0f;  // (fx .. h11 are not read before the first move)
@@ -279,17 +295,14 @@ __global__ void __launch_bounds__(THREADS) k_batch_simulate(const __grid_constan
             uint4 st = make_uint4(~0u, 0u, 0u, 0u), st1 = make_uint4(0u, 0u, 0u, 0u);
             if (mine) st = __ldg(reinterpret_cast<const uint4*>(q.starts) + 2u * ci);
             if (mine && q.texel) st1 = __ldg(reinterpret_cast<const uint4*>(q.starts) + 2u * ci + 1u);
-            const bool ok = mine && st.x != ~0u;
-            my_bad += (mine && !ok) ? 1u : 0u;
+            const bool ok = mine && st.x != ~0u;  // entries outside the grid: counted by k_batch_starts
+            AWO_FOLD_LANE(mine, q.max_steps);
             if (q.texel)  // warp-uniform
                 AWO_LANE_START_TEXEL(ok, st, st1, jj);
             else
                 AWO_LANE_START(ok, st, jj, q.W);
-            const bool cap0 = ok && q.max_steps == 0u;
-            my_cap += cap0 ? 1u : 0u;
             my_traj += ok ? 1u : 0u;  // particles are counted when they start
-            AWO_FOLD_MOVES();
-            live = live || (ok && !cap0);
+            live = live || ok;
             advance(cur_ci, cur_j, take, q.N);
             cur_t += take;
         }
@@ -302,7 +315,10 @@ __global__ void __launch_bounds__(THREADS) k_batch_simulate(const __grid_constan
         else
             AWO_MOVE_PAIR(q, (KeysWeyl{q.k0, q.k1}));
     }
-    if (cr >= 0) AWO_FLUSH_COUNTERS(a.hdr->stats[cr]);
+    if (cr >= 0) {
+        AWO_FOLD_LANE(true, q.max_steps);
+        AWO_FLUSH_COUNTERS(a.hdr->stats[cr]);
+    }
 }
 
 using BatchKernel = void (*)(BatchArgs);

@@ -99,21 +99,42 @@ __device__ __forceinline__ uint32_t release_count(const SimArgs& a)
 // Prologue: per release-list entry, the start record and the release visit
 // of all N particles (count += N; their energy is 0, so the maximum is
 // unchanged).  Grid-stride over the entries, whose number may be on the device.
-// TEXELS: the entries are texels of the release texture.
+// TEXELS: the entries are texels of the release texture.  It also counts the
+// particles of entries outside the grid (rejected) and, when max_steps = 0
+// (every particle capped at its release visit; the particle kernel is not
+// launched), the particles and caps.
 template <bool TEXELS>
 __global__ void __launch_bounds__(256) k_sim_starts(const __grid_constant__ SimArgs a)
 {
     const uint32_t n_cells = release_count(a);
+    unsigned long long good = 0ull, bad = 0ull;
     for (uint32_t ci = blockIdx.x * blockDim.x + threadIdx.x; ci < n_cells; ci += gridDim.x * blockDim.x) {
         const uint32_t entry = __ldg(a.cells + ci);
+        bool ok;
         if (TEXELS) {
             const TexelStart st = texel_start(a.h, a.W, a.H, a.tg, entry);
-            if (st.t != ~0u) atomicAdd(a.count + st.vcell, a.N);
+            ok = st.t != ~0u;
+            if (ok) atomicAdd(a.count + st.vcell, a.N);
             static_cast<TexelStart*>(a.starts)[ci] = st;
         } else {
             const CellStart st = cell_start(a.h, a.W, a.H, a.n_grid, entry);
-            if (st.xy != ~0u) atomicAdd(a.count + entry, a.N);
+            ok = st.xy != ~0u;
+            if (ok) atomicAdd(a.count + entry, a.N);
             static_cast<CellStart*>(a.starts)[ci] = st;
+        }
+        good += ok ? 1ull : 0ull;
+        bad += ok ? 0ull : 1ull;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        good += __shfl_xor_sync(0xffffffffu, good, o);
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicAdd(&a.ws->stats[5], bad * a.N);
+        if (good && a.max_steps == 0u) {
+            atomicAdd(&a.ws->stats[1], good * a.N);
+            atomicAdd(&a.ws->stats[3], good * a.N);
         }
     }
 }
@@ -179,17 +200,15 @@ __global__ void __launch_bounds__(SIM_THREADS) k_simulate(const __grid_constant_
                 } else {
                     if (mine) st = __ldg(reinterpret_cast<const uint4*>(a.starts) + ci);
                 }
+                // entries outside the grid are skipped here and counted by the prologue
                 const bool ok = mine && st.x != ~0u;
-                my_bad += (mine && !ok) ? 1u : 0u;  // release index outside the grid: skipped, reported
+                AWO_FOLD_LANE(mine, a.max_steps);
                 if (TEXELS)
                     AWO_LANE_START_TEXEL(ok, st, st1, jj);
                 else
                     AWO_LANE_START(ok, st, jj, a.W);
-                const bool cap0 = ok && a.max_steps == 0u;  // capped at the release visit
-                my_cap += cap0 ? 1u : 0u;
                 my_traj += ok ? 1u : 0u;  // particles are counted when they start
-                AWO_FOLD_MOVES();
-                live = live || (ok && !cap0);
+                live = live || ok;
                 advance(cur_ci, cur_j, take, a.N);
                 cur_t += take;
             }
@@ -200,6 +219,7 @@ __global__ void __launch_bounds__(SIM_THREADS) k_simulate(const __grid_constant_
         }
         AWO_MOVE_PAIR(a, a.keys);
     }
+    AWO_FOLD_LANE(true, a.max_steps);
     AWO_FLUSH_COUNTERS(a.ws->stats);
 }
 
@@ -372,7 +392,15 @@ extern "C" awo_status awo_simulate(const float* d_h, awo_grid g, const uint32_t*
 
     a.tex = dem_texture(d_h, g, s);
 
-    if (a.N > 0 && (n_cells_max > 0)) {
+    if (a.N > 0 && n_cells_max > 0 && a.max_steps == 0u) {  // every particle capped at its release visit
+        const unsigned pro_blocks = stream_blocks((int64_t)n_cells_max, 256);
+        if (texels)
+            k_sim_starts<true><<<pro_blocks, 256, 0, s>>>(a);
+        else
+            k_sim_starts<false><<<pro_blocks, 256, 0, s>>>(a);
+        awo_status st = launch_status();
+        if (st != AWO_OK) return st;
+    } else if (a.N > 0 && n_cells_max > 0) {
         const unsigned pro_blocks = stream_blocks((int64_t)n_cells_max, 256);
         const unsigned sms = (unsigned)sm_count();
         if (texels) {
