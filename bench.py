@@ -60,12 +60,15 @@ ALG_OPS_PER_VISIT = 126
 #   lts_frac: lts__throughput.avg.pct_of_peak_sustained_elapsed / 100, the L2's
 #     own utilisation against its peak -- the L2 gather/reduction roofline
 #     fraction of the kernel
-#   red_sectors, read_sectors: lts__t_sectors_op_red.sum and
-#     lts__t_sectors_op_read.sum (the visits' reductions and the footprint
-#     reads that miss in L1/texture cache)
+#   red_sectors, read_sectors: lts__t_sectors_srcunit_tex_op_red.sum and
+#     lts__t_sectors_srcunit_tex_op_read.sum (the visits' reductions, and the
+#     footprint reads that miss in the L1/texture cache, as the SMs send them)
+#   atomic_busy: lts__d_atomic_input_cycles_active.avg.pct_of_peak_sustained_elapsed
+#     / 100, the share of cycles the L2's reduction units take input
 KERNEL_COUNTERS: dict[str, dict[str, float]] = {
-    "843ee4cf528eda01": {"dram": (276.226048e6 + 55.794176e6) / 1754008332, "lts_frac": 0.64920426,
-                         "red_sectors": 3323214484 / 1754008332, "read_sectors": 19568102 / 1754008332},
+    "4f3655b0e9284d08": {"dram": (276.353536e6 + 55.977728e6) / 1754008332, "lts_frac": 0.67132645,
+                         "red_sectors": 2215786439 / 1754008332, "read_sectors": 15684411 / 1754008332,
+                         "atomic_busy": 0.45534489},
 }
 
 
@@ -389,6 +392,7 @@ def run_awo(args, R: Ranks):
     # gather/reduction roofline fraction; sector rates beside it
     l2 = {"frac": kc.get("lts_frac"), "source": "ncu lts__throughput.avg.pct_of_peak_sustained_elapsed, "
                                                 "6144^2 crop launch of the same kernel code",
+          "reduction_units_busy": kc.get("atomic_busy"),
           "red_sector_ops_per_s": kc["red_sectors"] * visits / sim_s if kc else None,
           "read_sectors_per_s": kc["read_sectors"] * visits / sim_s if kc else None,
           "random_access_probe": {"l2_red_per_s": peaks_probe["l2_red_per_s"],

@@ -42,6 +42,22 @@ awo_status awo_probe_l2_red(uint32_t* d_buf, uint32_t n_words, uint32_t iters, v
 /* Threads of the persistent probe grid on the current device. */
 uint64_t awo_probe_threads(void);
 
+/*
+ * Self-test of the particle kernels' normalisation (a check of this library's
+ * own arithmetic; the paper has no counterpart).  The kernels form
+ * 1 / sqrt(x) as two correctly rounded steps, s = RN(sqrt x) and
+ * r = RN(1 / s), with one hardware approximation each refined by Markstein's
+ * method inside [2^-100, 2^100] and by the IEEE intrinsics outside it.  This
+ * call compares that function with __frcp_rn(__fsqrt_rn(x)) bit for bit for
+ * x = every FP32 bit pattern b in [first, first + count) except +0 and -0,
+ * on the current device, and writes the number of mismatches to
+ * *d_mismatches (device uint64, 8-byte aligned, overwritten; zero means the
+ * particle kernels' directions are the IEEE ones on this GPU).  first = 0 and
+ * count = 2^32 check every input.  Asynchronous on `stream`.
+ * AWO_EINVAL: d_mismatches NULL or misaligned, or first + count > 2^32.
+ */
+awo_status awo_selftest_rcp_sqrt(uint32_t first, uint64_t count, uint64_t* d_mismatches, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -152,6 +152,7 @@ def lib() -> ctypes.CDLL:
         "awo_probe_l2_gather": (st, [vp, u32, u32, vp, vp]),
         "awo_probe_l2_red": (st, [vp, u32, u32, vp]),
         "awo_probe_threads": (ctypes.c_uint64, []),
+        "awo_selftest_rcp_sqrt": (st, [u32, ctypes.c_uint64, vp, vp]),
     }
     for name, (res, args) in protos.items():
         fn = getattr(L, name)
@@ -513,6 +514,12 @@ def awo_probe_l2_gather(buf: torch.Tensor, iters: int, sink: torch.Tensor, strea
 def awo_probe_l2_red(buf: torch.Tensor, iters: int, stream=None):
     _check(lib().awo_probe_l2_red(_dev(buf, torch.int32, None, "buf"), buf.numel(), int(iters), _stream(stream)),
            "awo_probe_l2_red")
+
+
+def awo_selftest_rcp_sqrt(first: int, count: int, out: torch.Tensor, stream=None):
+    """Mismatches (into out, int64 [1] on the device) of the kernels' 1/sqrt against the IEEE intrinsics."""
+    _check(lib().awo_selftest_rcp_sqrt(int(first), int(count), _dev(out, torch.int64, 1, "out"), _stream(stream)),
+           "awo_selftest_rcp_sqrt")
 
 
 def stats_dict(stats: torch.Tensor) -> dict:

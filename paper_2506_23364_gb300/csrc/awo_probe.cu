@@ -1,4 +1,5 @@
-// awo_probe.cu -- L2 scattered-load and scattered-reduction throughput probes.
+// awo_probe.cu -- L2 scattered-load and scattered-reduction throughput probes,
+// and the self-test of the particle kernels' correctly rounded normalisation.
 //
 // A persistent grid (SMs x 8 blocks of 256 threads, enough warps to cover L2
 // latency) issues independent, hashed 4-byte accesses into a buffer sized by
@@ -6,6 +7,7 @@
 // multiply-xorshift of (thread, round), so accesses spread over all L2
 // slices with no locality between lanes.
 #include "awo_internal.cuh"
+#include "awo_particle.cuh"
 #include "awo_probe.h"
 
 namespace awo {
@@ -51,9 +53,39 @@ __global__ void __launch_bounds__(PROBE_THREADS) k_probe_red(uint32_t* __restric
     }
 }
 
+// Every bit pattern b of [first, first + count) (but +-0): rcp_sqrt_rn(x)
+// against __frcp_rn(__fsqrt_rn(x)), bit for bit; one atomic per warp.
+__global__ void __launch_bounds__(256) k_selftest_rcp_sqrt(uint32_t first, unsigned long long count,
+                                                           unsigned long long* mismatches)
+{
+    unsigned long long bad = 0ull;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < count;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t bits = first + (uint32_t)i;
+        if ((bits & 0x7fffffffu) == 0u) continue;
+        const float x = __uint_as_float(bits);
+        bad += __float_as_uint(rcp_sqrt_rn(x)) != __float_as_uint(__frcp_rn(__fsqrt_rn(x))) ? 1ull : 0ull;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(mismatches, bad);
+}
+
 }  // namespace awo
 
 using namespace awo;
+
+extern "C" awo_status awo_selftest_rcp_sqrt(uint32_t first, uint64_t count, uint64_t* d_mismatches, void* stream)
+{
+    if (!d_mismatches || (((uintptr_t)d_mismatches) & 7u) != 0) return AWO_EINVAL;
+    if (count > (1ull << 32) - first) return AWO_EINVAL;
+    cudaStream_t s = as_stream(stream);
+    if (cudaMemsetAsync(d_mismatches, 0, sizeof(uint64_t), s) != cudaSuccess) return AWO_ECUDA;
+    if (count == 0) return AWO_OK;
+    k_selftest_rcp_sqrt<<<sm_count() * 8, 256, 0, s>>>(first, (unsigned long long)count,
+                                                       reinterpret_cast<unsigned long long*>(d_mismatches));
+    return launch_status();
+}
 
 extern "C" uint64_t awo_probe_threads(void)
 {

@@ -100,7 +100,7 @@ __device__ __forceinline__ void soft_particle(const SoftArgs& a, uint32_t ci, ui
         const float gn2 = __fadd_rn(__fmul_rn(ga, ga), __fmul_rn(gb, gb));
         float gx = dx, gy = dy;
         if (n != 0u && gn2 != 0.0f) {
-            const float ginv = __frcp_rn(__fsqrt_rn(gn2));
+            const float ginv = rcp_sqrt_rn(gn2);
             gx = __fmul_rn(-ga, ginv);
             gy = __fmul_rn(-gb, ginv);
         }
@@ -112,7 +112,7 @@ __device__ __forceinline__ void soft_particle(const SoftArgs& a, uint32_t ci, ui
         const float ry = __fadd_rn(__fadd_rn(__fmul_rn(a.P, dy), __fmul_rn(a.oneP, gy)), __fmul_rn(a.R, xiy));
         const float r2 = __fadd_rn(__fmul_rn(rx, rx), __fmul_rn(ry, ry));
         if (r2 == 0.0f) break;
-        const float rinv = __frcp_rn(__fsqrt_rn(r2));
+        const float rinv = rcp_sqrt_rn(r2);
         dx = __fmul_rn(rx, rinv);
         dy = __fmul_rn(ry, rinv);
         const float u1 = __fadd_rn(u, __fmul_rn(a.s, dx));

@@ -154,3 +154,14 @@ def test_release_texture_host_side(L):
     assert L.awo_soft_forward(fake, G16, fake, None, 4, fake, ctypes.byref(p), ctypes.c_float(1.0), fake, None,
                               fake, 1 << 20, None) == awo.AWO_EINVAL
     assert ctypes.sizeof(awo.SimParams) == 48 and awo.SimParams.release_log2.offset == 44
+
+
+def test_selftest_and_gather_path_host_validation(L):
+    fake = ctypes.c_void_p(256)
+    assert L.awo_selftest_rcp_sqrt(0, 1 << 32, None, None) == awo.AWO_EINVAL
+    assert L.awo_selftest_rcp_sqrt(0, 1 << 32, ctypes.c_void_p(260), None) == awo.AWO_EINVAL  # misaligned
+    assert L.awo_selftest_rcp_sqrt(1, 1 << 32, fake, None) == awo.AWO_EINVAL  # past 2^32
+    t = ctypes.c_int32(7)
+    assert L.awo_dem_gather_path(None, awo.grid(16, 16, 10.0), None, ctypes.byref(t)) == awo.AWO_EINVAL
+    assert L.awo_dem_gather_path(fake, awo.grid(0, 16, 10.0), None, ctypes.byref(t)) == awo.AWO_EINVAL
+    assert L.awo_dem_gather_path(fake, awo.grid(16, 16, 10.0), None, None) == awo.AWO_EINVAL
