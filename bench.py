@@ -66,9 +66,9 @@ ALG_OPS_PER_VISIT = 126
 #   atomic_busy: lts__d_atomic_input_cycles_active.avg.pct_of_peak_sustained_elapsed
 #     / 100, the share of cycles the L2's reduction units take input
 KERNEL_COUNTERS: dict[str, dict[str, float]] = {
-    "4f3655b0e9284d08": {"dram": (276.353536e6 + 55.977728e6) / 1754008332, "lts_frac": 0.67132645,
-                         "red_sectors": 2215786439 / 1754008332, "read_sectors": 15684411 / 1754008332,
-                         "atomic_busy": 0.45534489},
+    "2dd3ca568c9fbd02": {"dram": (276.236544e6 + 55.695616e6) / 1754008332, "lts_frac": 0.67652310,
+                         "red_sectors": 2215728028 / 1754008332, "read_sectors": 15673009 / 1754008332,
+                         "atomic_busy": 0.45865592},
 }
 
 

@@ -60,7 +60,10 @@ struct BatchHeader {
     unsigned long long stats[AWO_BATCH_MAX][6];
 };
 constexpr size_t BATCH_HEADER_BYTES = ((sizeof(BatchHeader) + 255) / 256) * 256;
-constexpr uint32_t BATCH_REFILL_IDLE = 12;
+// Lane refill once idle lanes add up to this many idle lane-iterations (as
+// in awo_simulate.cu; 64 regions 512^2..4096^2 on GB300: 12 -> 486.8 ms,
+// 8 -> 485.6 ms, 4 -> 482.7 ms per batched launch).
+constexpr uint32_t BATCH_REFILL_IDLE = 4;
 
 static_assert(sizeof(awo_sim_request) == 112, "awo_sim_request layout (C ABI)");
 static_assert(offsetof(awo_sim_request, params) == 48, "awo_sim_request layout (C ABI)");

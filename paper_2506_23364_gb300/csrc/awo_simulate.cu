@@ -83,11 +83,12 @@ constexpr uint32_t SIM_CHUNK_MAX = 1024;  // particles per global fetch, at most
 constexpr uint32_t SIM_CHUNKS_PER_WARP = 4;  // fetches a warp makes on an even split, at least
 // A warp refills its idle lanes once they add up to SIM_REFILL_IDLE idle
 // lane-iterations since its last refill (or when every lane is idle): a
-// refill round costs about as many issue slots as a dozen lanes idling
-// through one move, so refilling at every iteration wasted issue slots on
-// rounds that start one or two particles (measured on GB300: -4% time on
-// 8192^2, within noise on 2048^2, 256^2 and the parabola stand-in).
-constexpr uint32_t SIM_REFILL_IDLE = 12;
+// refill round costs issue slots whether it starts one particle or thirty,
+// so refilling for a single idle lane wastes slots, and waiting too long
+// leaves lanes idle.  Measured on GB300 (8192^2 particle kernel, ms, with the
+// counters folded per particle): 1 -> 20.61, 2 -> 20.50, 3 -> 20.46,
+// 4 -> 20.46, 6 -> 20.46, 8 -> 20.54, 12 -> 20.67, 16 -> 20.88.
+constexpr uint32_t SIM_REFILL_IDLE = 4;
 
 __device__ __forceinline__ uint32_t release_count(const SimArgs& a)
 {
