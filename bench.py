@@ -66,9 +66,9 @@ ALG_OPS_PER_VISIT = 126
 #   atomic_busy: lts__d_atomic_input_cycles_active.avg.pct_of_peak_sustained_elapsed
 #     / 100, the share of cycles the L2's reduction units take input
 KERNEL_COUNTERS: dict[str, dict[str, float]] = {
-    "89f69890714a7ff7": {"dram": (274.253056e6 + 55.590144e6) / 1754008332, "lts_frac": 0.68059102,
-                         "red_sectors": 2168093616 / 1754008332, "read_sectors": 14627100 / 1754008332,
-                         "atomic_busy": 0.46521993},
+    "1b0d024991a4a55b": {"dram": (274.944512e6 + 55.478528e6) / 1754008332, "lts_frac": 0.68372212,
+                         "red_sectors": 2168191075 / 1754008332, "read_sectors": 14621831 / 1754008332,
+                         "atomic_busy": 0.46696520},
 }
 
 
