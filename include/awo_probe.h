@@ -58,6 +58,18 @@ uint64_t awo_probe_threads(void);
  */
 awo_status awo_selftest_rcp_sqrt(uint32_t first, uint64_t count, uint64_t* d_mismatches, void* stream);
 
+/*
+ * Self-test of the particle kernels' visited cell (a check of this library's
+ * own arithmetic; the paper has no counterpart).  A visit goes to the cell
+ * whose centre is nearest, floor(u) + [u - floor(u) >= 1/2] per axis; the
+ * kernels form it as floor(u + 1/2) with the sum rounded toward zero.  This
+ * call compares the two for every FP32 bit pattern b in [first, first +
+ * count) whose value lies in [0, 2^23) (others are skipped) and writes the
+ * number of mismatches to *d_mismatches (as in awo_selftest_rcp_sqrt).
+ * AWO_EINVAL: d_mismatches NULL or misaligned, or first + count > 2^32.
+ */
+awo_status awo_selftest_visit_cell(uint32_t first, uint64_t count, uint64_t* d_mismatches, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -153,6 +153,7 @@ def lib() -> ctypes.CDLL:
         "awo_probe_l2_red": (st, [vp, u32, u32, vp]),
         "awo_probe_threads": (ctypes.c_uint64, []),
         "awo_selftest_rcp_sqrt": (st, [u32, ctypes.c_uint64, vp, vp]),
+        "awo_selftest_visit_cell": (st, [u32, ctypes.c_uint64, vp, vp]),
     }
     for name, (res, args) in protos.items():
         fn = getattr(L, name)
@@ -520,6 +521,12 @@ def awo_selftest_rcp_sqrt(first: int, count: int, out: torch.Tensor, stream=None
     """Mismatches (into out, int64 [1] on the device) of the kernels' 1/sqrt against the IEEE intrinsics."""
     _check(lib().awo_selftest_rcp_sqrt(int(first), int(count), _dev(out, torch.int64, 1, "out"), _stream(stream)),
            "awo_selftest_rcp_sqrt")
+
+
+def awo_selftest_visit_cell(first: int, count: int, out: torch.Tensor, stream=None):
+    """Mismatches (into out, int64 [1] on the device) of the kernels' visited cell against nearest-centre."""
+    _check(lib().awo_selftest_visit_cell(int(first), int(count), _dev(out, torch.int64, 1, "out"), _stream(stream)),
+           "awo_selftest_visit_cell")
 
 
 def stats_dict(stats: torch.Tensor) -> dict:

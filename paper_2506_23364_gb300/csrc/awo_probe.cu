@@ -71,6 +71,26 @@ __global__ void __launch_bounds__(256) k_selftest_rcp_sqrt(uint32_t first, unsig
     if ((threadIdx.x & 31) == 0 && bad) atomicAdd(mismatches, bad);
 }
 
+// Every FP32 position u in [first bits, first bits + count) that is >= 0:
+// visit_axis(u) against floor(u) + [u - floor(u) >= 1/2] in exact arithmetic
+// (the fraction u - floor(u) of a float below 2^23 is exact).
+__global__ void __launch_bounds__(256) k_selftest_visit(uint32_t first, unsigned long long count,
+                                                        unsigned long long* mismatches)
+{
+    unsigned long long bad = 0ull;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < count;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const float u = __uint_as_float(first + (uint32_t)i);
+        if (!(u >= 0.0f && u < 8388608.0f)) continue;
+        const float fl = floorf(u);
+        const int want = (int)fl + (__fsub_rn(u, fl) >= 0.5f ? 1 : 0);
+        bad += visit_axis(u) != want ? 1ull : 0ull;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(mismatches, bad);
+}
+
 }  // namespace awo
 
 using namespace awo;
@@ -108,5 +128,17 @@ extern "C" awo_status awo_probe_l2_red(uint32_t* d_buf, uint32_t n_words, uint32
     if (!d_buf || !pow2_ok(n_words) || iters == 0) return AWO_EINVAL;
     k_probe_red<<<sm_count() * PROBE_BLOCKS_PER_SM, PROBE_THREADS, 0, as_stream(stream)>>>(d_buf, n_words - 1u,
                                                                                            iters);
+    return launch_status();
+}
+
+extern "C" awo_status awo_selftest_visit_cell(uint32_t first, uint64_t count, uint64_t* d_mismatches, void* stream)
+{
+    if (!d_mismatches || (((uintptr_t)d_mismatches) & 7u) != 0) return AWO_EINVAL;
+    if (count > (1ull << 32) - first) return AWO_EINVAL;
+    cudaStream_t s = as_stream(stream);
+    if (cudaMemsetAsync(d_mismatches, 0, sizeof(uint64_t), s) != cudaSuccess) return AWO_ECUDA;
+    if (count == 0) return AWO_OK;
+    k_selftest_visit<<<sm_count() * 8, 256, 0, s>>>(first, (unsigned long long)count,
+                                                    reinterpret_cast<unsigned long long*>(d_mismatches));
     return launch_status();
 }
