@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "awo_internal.cuh"
+#include "awo_particle.cuh"  // rcp_sqrt_rn
 
 namespace awo {
 
@@ -77,7 +78,7 @@ __global__ void k_decode_u16(const uint16_t* __restrict__ q, int64_t n, float sc
 __device__ __forceinline__ void normal_of(float gx, float gy, float& nx, float& ny, float& nz, float& t2)
 {
     t2 = __fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy));
-    const float inv = __frcp_rn(__fsqrt_rn(__fadd_rn(t2, 1.0f)));
+    const float inv = rcp_sqrt_rn(__fadd_rn(t2, 1.0f));  // = __frcp_rn(__fsqrt_rn(.)) bit for bit, one branch
     nx = __fmul_rn(-gx, inv);
     ny = __fmul_rn(-gy, inv);
     nz = inv;
