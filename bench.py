@@ -66,9 +66,9 @@ ALG_OPS_PER_VISIT = 126
 #   atomic_busy: lts__d_atomic_input_cycles_active.avg.pct_of_peak_sustained_elapsed
 #     / 100, the share of cycles the L2's reduction units take input
 KERNEL_COUNTERS: dict[str, dict[str, float]] = {
-    "015078380c10f626": {"dram": (274.662912e6 + 55.616256e6) / 1754008332, "lts_frac": 0.68743106,
-                         "red_sectors": 2168036388 / 1754008332, "read_sectors": 14618374 / 1754008332,
-                         "atomic_busy": 0.46985835},
+    "1c0cc86155f971fe": {"dram": (274.137344e6 + 55.872768e6) / 1754008332, "lts_frac": 0.68618786,
+                         "red_sectors": 2168169469 / 1754008332, "read_sectors": 14619376 / 1754008332,
+                         "atomic_busy": 0.46897783},
 }
 
 
