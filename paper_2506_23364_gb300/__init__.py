@@ -154,6 +154,7 @@ def lib() -> ctypes.CDLL:
         "awo_probe_threads": (ctypes.c_uint64, []),
         "awo_selftest_rcp_sqrt": (st, [u32, ctypes.c_uint64, vp, vp]),
         "awo_selftest_visit_cell": (st, [u32, ctypes.c_uint64, vp, vp]),
+        "awo_selftest_div_rn": (st, [vp, u32, u32, vp, vp]),
     }
     for name, (res, args) in protos.items():
         fn = getattr(L, name)
@@ -527,6 +528,13 @@ def awo_selftest_visit_cell(first: int, count: int, out: torch.Tensor, stream=No
     """Mismatches (into out, int64 [1] on the device) of the kernels' visited cell against nearest-centre."""
     _check(lib().awo_selftest_visit_cell(int(first), int(count), _dev(out, torch.int64, 1, "out"), _stream(stream)),
            "awo_selftest_visit_cell")
+
+
+def awo_selftest_div_rn(divisors: torch.Tensor, span: int, out: torch.Tensor, stream=None):
+    """Mismatches of the compose pass's refined division against the IEEE intrinsic, into out (int64 [1])."""
+    _check(lib().awo_selftest_div_rn(_dev(divisors, torch.float32, None, "divisors"), int(divisors.numel()),
+                                     int(span), _dev(out, torch.int64, 1, "out"), _stream(stream)),
+           "awo_selftest_div_rn")
 
 
 def stats_dict(stats: torch.Tensor) -> dict:

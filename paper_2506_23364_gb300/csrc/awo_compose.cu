@@ -14,30 +14,31 @@ namespace awo {
 // above 255 give 255 (the saturating conversion of fmaxf(x, 0), capped).
 __device__ __forceinline__ uint32_t to_u8(float x) { return min(__float2uint_rn(fmaxf(x, 0.0f)), 255u); }
 
-// The colour ramp in shared memory: the stop values, and per segment k its
-// start value, width v[k+1] - v[k], start colour and colour step c[k+1] - c[k]
-// (the same roundings the per-texel formula makes; the colour step of 8-bit
-// colours is exact), so a texel reads its segment with two 16-byte loads.
+// The colour ramp in shared memory, per segment k: its start value, width
+// v[k+1] - v[k], start colour and colour step c[k+1] - c[k] (the same
+// roundings the per-texel formula makes; the colour step of 8-bit colours is
+// exact) -- two 16-byte loads per texel -- and RN(1 / width) for the division.
 struct RampSmem {
-    float value[16];
     float4 seg[15][2];  // {v0, dv, c0.r, c0.g}, {c0.b, dc.r, dc.g, dc.b}
+    float rcp[15];
 };
 
 // One texel: colour of value x, opacity from its count, over base texel b
-// (packed RGBA, little-endian bytes) when there is a base.  The segment is
-// the number of interior stops at or below x (stops strictly increase), a
-// loop of uniform trip count over the broadcast stop values.
-__device__ __forceinline__ uint32_t compose_one(const RampSmem& r, int n_stops, float v_first, float v_last,
-                                                float alpha, uint32_t count_min, float x, uint32_t count,
-                                                bool has_base, uint32_t b)
+// (packed RGBA, little-endian bytes) when HAS_BASE.  The segment is the
+// number of interior stops at or below x (stops strictly increase): NS - 2
+// compares against the stop values in the kernel's parameter bank.
+template <int NS, bool HAS_BASE>
+__device__ __forceinline__ uint32_t compose_one(const RampSmem& r, const awo_colormap& cm, float x, uint32_t count,
+                                                uint32_t b)
 {
-    if (!(x > v_first)) x = v_first;
-    if (x > v_last) x = v_last;
+    if (!(x > cm.value[0])) x = cm.value[0];
+    if (x > cm.value[NS - 1]) x = cm.value[NS - 1];
     int k = 0;
-    for (int j = 1; j < n_stops - 1; ++j) k += x >= r.value[j] ? 1 : 0;
+#pragma unroll
+    for (int j = 1; j < NS - 1; ++j) k += x >= cm.value[j] ? 1 : 0;
     const float4 s0 = r.seg[k][0], s1 = r.seg[k][1];
-    const float t = __fdiv_rn(__fsub_rn(x, s0.x), s0.y);
-    const float a = count >= count_min ? alpha : 0.0f;
+    const float t = div_rn_by_rcp(__fsub_rn(x, s0.x), s0.y, r.rcp[k]);  // = __fdiv_rn(x - v0, dv)
+    const float a = count >= cm.count_min ? cm.alpha : 0.0f;
     const float col[3] = {__fadd_rn(s0.z, __fmul_rn(t, s1.y)), __fadd_rn(s0.w, __fmul_rn(t, s1.z)),
                           __fadd_rn(s1.x, __fmul_rn(t, s1.w))};
     const float na = __fsub_rn(1.0f, a);
@@ -45,54 +46,60 @@ __device__ __forceinline__ uint32_t compose_one(const RampSmem& r, int n_stops, 
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const float bc = (float)((b >> (8 * c)) & 0xffu);
-        const uint32_t ch = has_base ? to_u8(__fadd_rn(__fmul_rn(a, col[c]), __fmul_rn(na, bc))) : to_u8(col[c]);
+        const uint32_t ch = HAS_BASE ? to_u8(__fadd_rn(__fmul_rn(a, col[c]), __fmul_rn(na, bc))) : to_u8(col[c]);
         o |= ch << (8 * c);
     }
-    const uint32_t oa = has_base ? (b >> 24) : to_u8(__fmul_rn(255.0f, a));
+    const uint32_t oa = HAS_BASE ? (b >> 24) : to_u8(__fmul_rn(255.0f, a));
     return o | (oa << 24);
 }
 
 // Four texels per thread (float4 / uint4 loads, uint4 store) when every
-// buffer is 16-byte aligned, then a scalar tail.
+// buffer is 16-byte aligned, then a scalar tail.  One instance per stop count
+// and base / no base: the stop compares unroll, and no texel selects between
+// the two blends.
+template <int NS, bool HAS_BASE>
 __global__ void k_compose(const float* __restrict__ value, const uint32_t* __restrict__ count, int64_t n,
                           const __grid_constant__ awo_colormap cm, const uint8_t* __restrict__ base,
                           uint8_t* __restrict__ out, bool vec4)
 {
     __shared__ RampSmem ramp;
-    for (int i = threadIdx.x; i < 16; i += blockDim.x) {
-        ramp.value[i] = cm.value[i];
-        if (i + 1 < cm.n_stops) {
-            const float c0r = (float)cm.rgb[i][0], c0g = (float)cm.rgb[i][1], c0b = (float)cm.rgb[i][2];
-            ramp.seg[i][0] = make_float4(cm.value[i], __fsub_rn(cm.value[i + 1], cm.value[i]), c0r, c0g);
-            ramp.seg[i][1] = make_float4(c0b, __fsub_rn((float)cm.rgb[i + 1][0], c0r),
-                                         __fsub_rn((float)cm.rgb[i + 1][1], c0g),
-                                         __fsub_rn((float)cm.rgb[i + 1][2], c0b));
-        }
+    for (int i = threadIdx.x; i < NS - 1; i += blockDim.x) {
+        const float c0r = (float)cm.rgb[i][0], c0g = (float)cm.rgb[i][1], c0b = (float)cm.rgb[i][2];
+        const float dv = __fsub_rn(cm.value[i + 1], cm.value[i]);
+        ramp.seg[i][0] = make_float4(cm.value[i], dv, c0r, c0g);
+        ramp.seg[i][1] = make_float4(c0b, __fsub_rn((float)cm.rgb[i + 1][0], c0r),
+                                     __fsub_rn((float)cm.rgb[i + 1][1], c0g), __fsub_rn((float)cm.rgb[i + 1][2], c0b));
+        ramp.rcp[i] = __frcp_rn(dv);
     }
     __syncthreads();
-    const int ns = cm.n_stops;
-    const float v_first = cm.value[0], v_last = cm.value[ns - 1];
-    const float alpha = cm.alpha;
-    const uint32_t cmin = cm.count_min;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool has_base = base != nullptr;
     const uint32_t* base32 = reinterpret_cast<const uint32_t*>(base);
     uint32_t* out32 = reinterpret_cast<uint32_t*>(out);
     const int64_t n4 = vec4 ? n / 4 : 0;
     for (int64_t q = tid; q < n4; q += stride) {
         const float4 v = __ldg(reinterpret_cast<const float4*>(value) + q);
         const uint4 c = __ldg(reinterpret_cast<const uint4*>(count) + q);
-        const uint4 b = has_base ? __ldg(reinterpret_cast<const uint4*>(base32) + q) : make_uint4(0u, 0u, 0u, 0u);
+        const uint4 b = HAS_BASE ? __ldg(reinterpret_cast<const uint4*>(base32) + q) : make_uint4(0u, 0u, 0u, 0u);
         reinterpret_cast<uint4*>(out32)[q] =
-            make_uint4(compose_one(ramp, ns, v_first, v_last, alpha, cmin, v.x, c.x, has_base, b.x),
-                       compose_one(ramp, ns, v_first, v_last, alpha, cmin, v.y, c.y, has_base, b.y),
-                       compose_one(ramp, ns, v_first, v_last, alpha, cmin, v.z, c.z, has_base, b.z),
-                       compose_one(ramp, ns, v_first, v_last, alpha, cmin, v.w, c.w, has_base, b.w));
+            make_uint4(compose_one<NS, HAS_BASE>(ramp, cm, v.x, c.x, b.x),
+                       compose_one<NS, HAS_BASE>(ramp, cm, v.y, c.y, b.y),
+                       compose_one<NS, HAS_BASE>(ramp, cm, v.z, c.z, b.z),
+                       compose_one<NS, HAS_BASE>(ramp, cm, v.w, c.w, b.w));
     }
     for (int64_t i = 4 * n4 + tid; i < n; i += stride)
-        out32[i] = compose_one(ramp, ns, v_first, v_last, alpha, cmin, value[i], count[i], has_base,
-                               has_base ? base32[i] : 0u);
+        out32[i] = compose_one<NS, HAS_BASE>(ramp, cm, value[i], count[i], HAS_BASE ? base32[i] : 0u);
+}
+
+template <int NS>
+static void launch_compose(const float* v, const uint32_t* c, int64_t n, const awo_colormap& cm, const uint8_t* b,
+                           uint8_t* o, bool vec4, cudaStream_t s)
+{
+    const unsigned blocks = stream_blocks(vec4 ? n / 4 + 1 : n, 256);
+    if (b)
+        k_compose<NS, true><<<blocks, 256, 0, s>>>(v, c, n, cm, b, o, vec4);
+    else
+        k_compose<NS, false><<<blocks, 256, 0, s>>>(v, c, n, cm, b, o, vec4);
 }
 
 __device__ __forceinline__ float smooth_step(float e0, float e1, float x)
@@ -149,8 +156,18 @@ extern "C" awo_status awo_compose(const float* d_value, const uint32_t* d_count,
     const int64_t n = cells_of(g);
     const bool vec4 = ((((uintptr_t)d_value) | ((uintptr_t)d_count) | ((uintptr_t)d_base_rgba) |
                         ((uintptr_t)d_out_rgba)) & 15u) == 0;
-    k_compose<<<stream_blocks(vec4 ? n / 4 + 1 : n, 256), 256, 0, as_stream(stream)>>>(d_value, d_count, n, *cm,
-                                                                                        d_base_rgba, d_out_rgba, vec4);
+    const cudaStream_t s = as_stream(stream);
+    switch (cm->n_stops) {
+#define AWO_COMPOSE_NS(K)                                                                              \
+    case K:                                                                                            \
+        launch_compose<K>(d_value, d_count, n, *cm, d_base_rgba, d_out_rgba, vec4, s);                 \
+        break;
+        AWO_COMPOSE_NS(2) AWO_COMPOSE_NS(3) AWO_COMPOSE_NS(4) AWO_COMPOSE_NS(5) AWO_COMPOSE_NS(6)
+        AWO_COMPOSE_NS(7) AWO_COMPOSE_NS(8) AWO_COMPOSE_NS(9) AWO_COMPOSE_NS(10) AWO_COMPOSE_NS(11)
+        AWO_COMPOSE_NS(12) AWO_COMPOSE_NS(13) AWO_COMPOSE_NS(14) AWO_COMPOSE_NS(15) AWO_COMPOSE_NS(16)
+#undef AWO_COMPOSE_NS
+        default: return AWO_EINVAL;
+    }
     return launch_status();
 }
 

@@ -82,6 +82,31 @@ inline bool sim_params_ok(const awo_sim_params* p, awo_grid g)
     return sim_params_ok(p, g.cell_size) && release_texture_dims(g, p->release_log2, &wr, &hr);
 }
 
+#ifdef __CUDACC__
+// a / b rounded to nearest (the value of __fdiv_rn(a, b)) from y = RN(1 / b),
+// the correctly rounded reciprocal, by two corrections of the quotient with
+// exact FMA remainders, q' = q + (a - b q) y: the first takes q0 = RN(a y) to
+// a faithful quotient (relative error about 2^-47 before its rounding), and
+// the second turns a faithful quotient into the correctly rounded one
+// (Markstein's theorem: P. Markstein, IBM J. Res. Dev. 34 (1990) 111-119;
+// M. Cornea, J. Harrison, P. T. P. Tang, Scientific Computing on
+// Itanium-based Systems, 2002).  The theorem needs every intermediate value
+// normal and every remainder exact: a = +0 or a in [2^-60, 2^60], b in
+// [2^-60, 2^60]; elsewhere the intrinsic gives the value.
+// awo_selftest_div_rn compares this function with the intrinsic on the
+// running GPU.
+__device__ __forceinline__ float div_rn_by_rcp(float a, float b, float y)
+{
+    const uint32_t ab = __float_as_uint(a);
+    const bool fast = (ab == 0u || (ab >= 0x21800000u && ab <= 0x5d800000u)) &&  // +0 or [2^-60, 2^60]
+                      (b >= 0x1p-60f && b <= 0x1p60f);
+    if (!fast) return __fdiv_rn(a, b);
+    const float q0 = __fmul_rn(a, y);
+    const float q1 = __fmaf_rn(__fmaf_rn(-b, q0, a), y, q0);
+    return __fmaf_rn(__fmaf_rn(-b, q1, a), y, q1);
+}
+#endif
+
 // Texture view of the DEM buffer d_h of grid g for the particle kernels'
 // footprint gathers, or 0 when the grid is small, the buffer or row pitch is
 // not texture-aligned, the view table is full, or a new view would be needed

@@ -107,6 +107,43 @@ extern "C" awo_status awo_selftest_rcp_sqrt(uint32_t first, uint64_t count, uint
     return launch_status();
 }
 
+// Every divisor b of the list (positive, finite) and every FP32 a with bits
+// in [bits(b) - span, bits(b)] (at least +0): div_rn_by_rcp against the
+// intrinsic.  Divisors in turn, each spread over the whole grid.
+__global__ void __launch_bounds__(256) k_selftest_div(const float* __restrict__ divisors, uint32_t n_div,
+                                                      uint32_t span, unsigned long long* mismatches)
+{
+    unsigned long long bad = 0ull;
+    const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (uint32_t d = 0; d < n_div; ++d) {
+        const float b = __ldg(divisors + d);
+        if (!(b > 0.0f && b <= 3.4028234663852886e38f)) continue;
+        const uint32_t bb = __float_as_uint(b);
+        const uint32_t lo = span >= bb ? 0u : bb - span;
+        const float y = __frcp_rn(b);
+        for (unsigned long long i = tid; i <= (unsigned long long)(bb - lo); i += stride) {
+            const float a = __uint_as_float(lo + (uint32_t)i);
+            bad += __float_as_uint(div_rn_by_rcp(a, b, y)) != __float_as_uint(__fdiv_rn(a, b)) ? 1ull : 0ull;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(mismatches, bad);
+}
+
+extern "C" awo_status awo_selftest_div_rn(const float* d_divisors, uint32_t n_divisors, uint32_t span,
+                                          uint64_t* d_mismatches, void* stream)
+{
+    if (!d_divisors || (((uintptr_t)d_divisors) & 3u) != 0 || n_divisors == 0) return AWO_EINVAL;
+    if (!d_mismatches || (((uintptr_t)d_mismatches) & 7u) != 0) return AWO_EINVAL;
+    cudaStream_t s = as_stream(stream);
+    if (cudaMemsetAsync(d_mismatches, 0, sizeof(uint64_t), s) != cudaSuccess) return AWO_ECUDA;
+    k_selftest_div<<<sm_count() * 8, 256, 0, s>>>(d_divisors, n_divisors, span,
+                                                  reinterpret_cast<unsigned long long*>(d_mismatches));
+    return launch_status();
+}
+
 extern "C" uint64_t awo_probe_threads(void)
 {
     return (uint64_t)sm_count() * PROBE_BLOCKS_PER_SM * PROBE_THREADS;

@@ -51,21 +51,56 @@ def test_parabola_standin_bitexact():
     assert got["stats"]["n_traj"] == 6144 and got["stats"]["total_steps"] == st["total_steps"]
 
 
+RAMPS = {
+    "velocity5": awo.VELOCITY_STOPS,
+    "two": [(0.0, (0, 0, 0)), (1.0, (255, 128, 1))],
+    "ramp16": [(float(3 * i * i), (16 * i, 255 - 16 * i, (37 * i) % 256)) for i in range(16)],
+    "huge": [(-1.0e30, (10, 20, 30)), (0.0, (200, 0, 100)), (1.0e30, (0, 255, 0))],  # widths above 2^60
+    "tiny": [(0.0, (0, 0, 255)), (1.0e-20, (255, 0, 0)), (2.5e-20, (0, 255, 0)), (6.0e-20, (9, 9, 9))],
+}
+
+
+@pytest.mark.parametrize("ramp", sorted(RAMPS))
 @pytest.mark.parametrize("with_base", [False, True])
-def test_compose_bitexact(with_base):
+def test_compose_bitexact(ramp, with_base):
+    """Every stop count has its own kernel instance and the division of the
+    ramp has a fast path for widths in [2^-60, 2^60]: stop counts 2..16,
+    widths inside and outside that range, values on the stops, between them
+    and beyond both ends."""
+    stops = RAMPS[ramp]
     rng = np.random.default_rng(5)
     H, W = 301, 257
-    v = rng.uniform(-5, 80, (H, W)).astype(np.float32)
-    v[rng.random((H, W)) < 0.05] = 10.0  # exactly on a stop
+    lo, hi = stops[0][0], stops[-1][0]
+    pad = 0.1 * (hi - lo)
+    v = rng.uniform(lo - pad, hi + pad, (H, W)).astype(np.float32)
+    on = rng.random((H, W)) < 0.05
+    v[on] = np.array([s[0] for s in stops], dtype=np.float32)[rng.integers(0, len(stops), int(on.sum()))]
+    v[rng.random((H, W)) < 0.02] = np.float32(lo)
     cnt = rng.integers(0, 5, (H, W)).astype(np.uint32)
     base = rng.integers(0, 256, (H, W, 4)).astype(np.uint8) if with_base else None
     g = awo.grid(W, H, 10.0)
-    cm = awo.Colormap.make(awo.VELOCITY_STOPS, alpha=0.7, count_min=2)
+    cm = awo.Colormap.make(stops, alpha=0.7, count_min=2)
     out = torch.empty((H, W, 4), dtype=torch.uint8, device="cuda")
     awo.awo_compose(torch.from_numpy(v).cuda(), torch.from_numpy(cnt.view(np.int32)).cuda(), g, cm,
                     torch.from_numpy(base).cuda() if with_base else None, out)
-    want = oracle.compose(v, cnt, awo.VELOCITY_STOPS, 0.7, 2, base)
+    want = oracle.compose(v, cnt, stops, 0.7, 2, base)
     assert np.array_equal(out.cpu().numpy(), want)
+
+
+def test_compose_unaligned_buffers():
+    """Buffers off the 16-byte boundary take the one-texel path."""
+    rng = np.random.default_rng(8)
+    H, W = 37, 53
+    v = rng.uniform(-5, 80, (H * W + 1,)).astype(np.float32)
+    cnt = rng.integers(0, 5, (H * W + 1,)).astype(np.uint32)
+    base = rng.integers(0, 256, (H * W + 1, 4)).astype(np.uint8)
+    dv, dc, db = torch.from_numpy(v).cuda(), torch.from_numpy(cnt.view(np.int32)).cuda(), torch.from_numpy(base).cuda()
+    out = torch.empty((H * W + 1, 4), dtype=torch.uint8, device="cuda")
+    cm = awo.Colormap.make(awo.VELOCITY_STOPS, alpha=0.7, count_min=2)
+    awo.awo_compose(dv[1:], dc[1:], awo.grid(W, H, 10.0), cm, db[1:], out[1:])
+    want = oracle.compose(v[1:].reshape(H, W), cnt[1:].reshape(H, W), awo.VELOCITY_STOPS, 0.7, 2,
+                          base[1:].reshape(H, W, 4))
+    assert np.array_equal(out[1:].cpu().numpy().reshape(H, W, 4), want)
 
 
 def test_snow_cover_bitexact():
