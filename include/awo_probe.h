@@ -75,13 +75,14 @@ awo_status awo_selftest_visit_cell(uint32_t first, uint64_t count, uint64_t* d_m
  * of this library's own arithmetic; the paper has no counterpart).  The
  * colour ramp divides by each segment's width through its correctly rounded
  * reciprocal and two quotient corrections (Markstein's method) instead of
- * the IEEE division intrinsic.  For each of the n_divisors divisors b in
+ * the IEEE division intrinsic, and so do the normals' central differences
+ * (dividends of either sign).  For each of the n_divisors divisors b in
  * d_divisors (device, FP32; entries that are not positive and finite are
  * skipped), this call compares the two for every FP32 a whose bit pattern
  * lies in [bits(b) - span, bits(b)] (clamped at +0: span >= bits(b) covers
- * all of [0, b], span = 2^23 the binade below b) and writes the number of
- * mismatches to *d_mismatches (device uint64, 8-byte aligned; set to 0
- * first), in stream order.
+ * all of [0, b], span = 2^23 the binade below b), and for -a, and writes the
+ * number of mismatches (bit patterns that differ) to *d_mismatches (device
+ * uint64, 8-byte aligned; set to 0 first), in stream order.
  * AWO_EINVAL: d_divisors or d_mismatches NULL or misaligned, n_divisors = 0.
  */
 awo_status awo_selftest_div_rn(const float* d_divisors, uint32_t n_divisors, uint32_t span, uint64_t* d_mismatches,

@@ -37,7 +37,7 @@ __device__ __forceinline__ uint32_t compose_one(const RampSmem& r, const awo_col
 #pragma unroll
     for (int j = 1; j < NS - 1; ++j) k += x >= cm.value[j] ? 1 : 0;
     const float4 s0 = r.seg[k][0], s1 = r.seg[k][1];
-    const float t = div_rn_by_rcp(__fsub_rn(x, s0.x), s0.y, r.rcp[k]);  // = __fdiv_rn(x - v0, dv)
+    const float t = div_rn_by_rcp<false>(__fsub_rn(x, s0.x), s0.y, r.rcp[k]);  // = __fdiv_rn(x - v0, dv)
     const float a = count >= cm.count_min ? cm.alpha : 0.0f;
     const float col[3] = {__fadd_rn(s0.z, __fmul_rn(t, s1.y)), __fadd_rn(s0.w, __fmul_rn(t, s1.z)),
                           __fadd_rn(s1.x, __fmul_rn(t, s1.w))};

@@ -91,19 +91,24 @@ inline bool sim_params_ok(const awo_sim_params* p, awo_grid g)
 // (Markstein's theorem: P. Markstein, IBM J. Res. Dev. 34 (1990) 111-119;
 // M. Cornea, J. Harrison, P. T. P. Tang, Scientific Computing on
 // Itanium-based Systems, 2002).  The theorem needs every intermediate value
-// normal and every remainder exact: a = +0 or a in [2^-60, 2^60], b in
-// [2^-60, 2^60]; elsewhere the intrinsic gives the value.
+// normal and every remainder exact: |a| = 0 or in [2^-60, 2^60], b in
+// [2^-60, 2^60]; elsewhere the intrinsic gives the value.  SIGNED: a of
+// either sign (rounding to nearest is symmetric: the quotient of |a| takes
+// a's sign); otherwise negative a and -0 take the intrinsic.
 // awo_selftest_div_rn compares this function with the intrinsic on the
 // running GPU.
+template <bool SIGNED = false>
 __device__ __forceinline__ float div_rn_by_rcp(float a, float b, float y)
 {
-    const uint32_t ab = __float_as_uint(a);
-    const bool fast = (ab == 0u || (ab >= 0x21800000u && ab <= 0x5d800000u)) &&  // +0 or [2^-60, 2^60]
+    const uint32_t ab = __float_as_uint(a) & (SIGNED ? 0x7fffffffu : 0xffffffffu);
+    const bool fast = (ab == 0u || (ab >= 0x21800000u && ab <= 0x5d800000u)) &&  // |a|: 0 or [2^-60, 2^60]
                       (b >= 0x1p-60f && b <= 0x1p60f);
     if (!fast) return __fdiv_rn(a, b);
-    const float q0 = __fmul_rn(a, y);
-    const float q1 = __fmaf_rn(__fmaf_rn(-b, q0, a), y, q0);
-    return __fmaf_rn(__fmaf_rn(-b, q1, a), y, q1);
+    const float m = __uint_as_float(ab);
+    const float q0 = __fmul_rn(m, y);
+    const float q1 = __fmaf_rn(__fmaf_rn(-b, q0, m), y, q0);
+    const float q2 = __fmaf_rn(__fmaf_rn(-b, q1, m), y, q1);
+    return SIGNED ? __uint_as_float(__float_as_uint(q2) | (__float_as_uint(a) & 0x80000000u)) : q2;
 }
 #endif
 

@@ -108,8 +108,9 @@ extern "C" awo_status awo_selftest_rcp_sqrt(uint32_t first, uint64_t count, uint
 }
 
 // Every divisor b of the list (positive, finite) and every FP32 a with bits
-// in [bits(b) - span, bits(b)] (at least +0): div_rn_by_rcp against the
-// intrinsic.  Divisors in turn, each spread over the whole grid.
+// in [bits(b) - span, bits(b)] (at least +0): div_rn_by_rcp of a (unsigned and
+// signed forms) and of -a (signed form) against the intrinsic.  Divisors in
+// turn, each spread over the whole grid.
 __global__ void __launch_bounds__(256) k_selftest_div(const float* __restrict__ divisors, uint32_t n_div,
                                                       uint32_t span, unsigned long long* mismatches)
 {
@@ -124,7 +125,10 @@ __global__ void __launch_bounds__(256) k_selftest_div(const float* __restrict__ 
         const float y = __frcp_rn(b);
         for (unsigned long long i = tid; i <= (unsigned long long)(bb - lo); i += stride) {
             const float a = __uint_as_float(lo + (uint32_t)i);
-            bad += __float_as_uint(div_rn_by_rcp(a, b, y)) != __float_as_uint(__fdiv_rn(a, b)) ? 1ull : 0ull;
+            const uint32_t want = __float_as_uint(__fdiv_rn(a, b)), want_neg = __float_as_uint(__fdiv_rn(-a, b));
+            bad += __float_as_uint(div_rn_by_rcp<false>(a, b, y)) != want ? 1ull : 0ull;
+            bad += __float_as_uint(div_rn_by_rcp<true>(a, b, y)) != want ? 1ull : 0ull;
+            bad += __float_as_uint(div_rn_by_rcp<true>(-a, b, y)) != want_neg ? 1ull : 0ull;
         }
     }
 #pragma unroll

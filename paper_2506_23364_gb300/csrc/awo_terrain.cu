@@ -123,11 +123,12 @@ __global__ void __launch_bounds__(256) k_normals(const HeightSrc<FROM_U16> h, in
     const uint32_t runs = (uint32_t)((W + 3) >> 2);
     const uint32_t items = runs * (uint32_t)H;
     const float den1 = cs, den2 = __fmul_rn(cs, 2.0f);
+    const float rden1 = __frcp_rn(den1), rden2 = __frcp_rn(den2);  // the divisions: div_rn_by_rcp, = __fdiv_rn
     for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
         const int y = (int)(it / runs);
         const int x0 = (int)(it - (uint32_t)y * runs) * 4;
         const int yl = y > 0 ? y - 1 : 0, yr = y < H - 1 ? y + 1 : H - 1;
-        const float deny = yr - yl == 2 ? den2 : den1;
+        const float deny = yr - yl == 2 ? den2 : den1, rdeny = yr - yl == 2 ? rden2 : rden1;
         const int64_t row = (int64_t)y * W;
         if (vec4) {
             const float4 c = h.at4(row + x0);
@@ -146,8 +147,10 @@ __global__ void __launch_bounds__(256) k_normals(const HeightSrc<FROM_U16> h, in
                 float gx = 0.0f, gy = 0.0f;
                 const float h_r = x < W - 1 ? hc[k + 2] : hc[k + 1];
                 const float h_l = x > 0 ? hc[k] : hc[k + 1];
-                if (xr > xl) gx = __fdiv_rn(__fsub_rn(h_r, h_l), xr - xl == 2 ? den2 : den1);
-                if (yr > yl) gy = __fdiv_rn(__fsub_rn(hd[k], hu[k]), deny);
+                if (xr > xl)
+                    gx = xr - xl == 2 ? div_rn_by_rcp<true>(__fsub_rn(h_r, h_l), den2, rden2)
+                                      : div_rn_by_rcp<true>(__fsub_rn(h_r, h_l), den1, rden1);
+                if (yr > yl) gy = div_rn_by_rcp<true>(__fsub_rn(hd[k], hu[k]), deny, rdeny);
                 normal_of(gx, gy, o_nx[k], o_ny[k], o_nz[k], o_t2[k]);
             }
             if (nrm) {
@@ -166,8 +169,12 @@ __global__ void __launch_bounds__(256) k_normals(const HeightSrc<FROM_U16> h, in
             for (int x = x0; x < x_end; ++x) {
                 const int xl = x > 0 ? x - 1 : 0, xr = x < W - 1 ? x + 1 : W - 1;
                 float gx = 0.0f, gy = 0.0f;
-                if (xr > xl) gx = __fdiv_rn(__fsub_rn(h.at(row + xr), h.at(row + xl)), xr - xl == 2 ? den2 : den1);
-                if (yr > yl) gy = __fdiv_rn(__fsub_rn(h.at((int64_t)yr * W + x), h.at((int64_t)yl * W + x)), deny);
+                if (xr > xl)
+                    gx = div_rn_by_rcp<true>(__fsub_rn(h.at(row + xr), h.at(row + xl)), xr - xl == 2 ? den2 : den1,
+                                             xr - xl == 2 ? rden2 : rden1);
+                if (yr > yl)
+                    gy = div_rn_by_rcp<true>(__fsub_rn(h.at((int64_t)yr * W + x), h.at((int64_t)yl * W + x)), deny,
+                                             rdeny);
                 float nx, ny, nz, t2;
                 normal_of(gx, gy, nx, ny, nz, t2);
                 const int64_t i = row + x;
