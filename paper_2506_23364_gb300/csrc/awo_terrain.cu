@@ -367,12 +367,40 @@ __global__ void __launch_bounds__(1024) k_release_scan(const uint32_t* __restric
             }
         }
     } else {
-        int s = 0;
-        for (int t = lo; t < hi; ++t) s += (int)tile_count[t];
-        int run = block_exclusive_scan(s, &total);
-        for (int t = lo; t < hi; ++t) {
-            tile_offset[t] = (uint32_t)run;
-            run += (int)tile_count[t];
+        // more than 16 tiles a thread (release textures): two passes over the
+        // thread's range, 16-byte loads unrolled so that several are in flight
+        const bool vec = (per & 3) == 0 && (((uintptr_t)tile_count) & 15u) == 0 &&
+                         (((uintptr_t)tile_offset) & 15u) == 0 && hi - lo == per;
+        const uint4* src = reinterpret_cast<const uint4*>(tile_count + lo);
+        uint32_t s = 0u;
+        if (vec) {
+#pragma unroll 2
+            for (int q = 0; q < per / 4; ++q) {
+                const uint4 v = __ldg(src + q);
+                s += v.x + v.y + v.z + v.w;
+            }
+        } else {
+            for (int t = lo; t < hi; ++t) s += tile_count[t];
+        }
+        uint32_t run = (uint32_t)block_exclusive_scan((int)s, &total);
+        if (vec) {
+            uint4* dst = reinterpret_cast<uint4*>(tile_offset + lo);
+#pragma unroll 2
+            for (int q = 0; q < per / 4; ++q) {
+                const uint4 v = __ldg(src + q);
+                uint4 o;
+                o.x = run;
+                o.y = o.x + v.x;
+                o.z = o.y + v.y;
+                o.w = o.z + v.z;
+                run = o.w + v.w;
+                dst[q] = o;
+            }
+        } else {
+            for (int t = lo; t < hi; ++t) {
+                tile_offset[t] = run;
+                run += tile_count[t];
+            }
         }
     }
     if (threadIdx.x == 0) *d_n = (uint32_t)total;

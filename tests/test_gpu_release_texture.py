@@ -181,3 +181,19 @@ def test_batched_mixed_release_resolutions(refill):
         assert np.array_equal(got["count"], oracle.counts_u32(c64)), i
         assert np.array_equal(got["maxe"], maxe), i
         assert b.stats_list()[i]["total_steps"] == st["total_steps"], i
+
+
+@pytest.mark.parametrize("shape,r", [((4096, 4096), 2), ((4160, 4096), 1)])
+def test_release_texture_many_tiles(shape, r):
+    """Textures of more than 16384 tiles of 4096 texels take the tile-count
+    scan's wide path: 65536 tiles (64 a thread, 16-byte loads) and 16640
+    (17 a thread, one by one)."""
+    H, W = shape
+    h = inputs.fbm(max(H, W), 0.8, seed=77, relief=3000.0)[:H, :W].astype(np.float32)
+    g, t2 = _tan2(h, 10.0)
+    wr, hr = awo.awo_release_texture_dims(g, r)
+    assert (wr * hr + 4095) // 4096 > 16384
+    m_ref, tex_ref = oracle.release_texture(t2.cpu().numpy(), r, 30.0, 45.0)
+    m_got, tex_got = _gpu_release_texture(t2, g, r, 30.0, 45.0)
+    assert np.array_equal(m_got, m_ref)
+    assert np.array_equal(tex_got, tex_ref)
