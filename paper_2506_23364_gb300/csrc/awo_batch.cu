@@ -6,7 +6,8 @@
 //   k_batch_prepare  one block: release counts (possibly on the device), the
 //                    chunk size, the prefix sums of cells and of particle
 //                    chunks over requests, zeroed counters;
-//   k_batch_starts   per release cell of every request: its start record and
+//   k_batch_starts   per release cell of every request: its start record (in
+//                    the processing order of awo_particle.cuh) and
 //                    the release visits of its particles;
 //   k_batch_simulate persistent: warps take chunks of consecutive particles
 //                    from one global counter over all requests.  A warp
@@ -58,6 +59,7 @@ struct BatchHeader {
     uint32_t chunk;                                    // particles per chunk
     uint32_t pad;
     unsigned long long stats[AWO_BATCH_MAX][6];
+    uint32_t order_stride[AWO_BATCH_MAX];              // processing order of each request's entries
 };
 constexpr size_t BATCH_HEADER_BYTES = ((sizeof(BatchHeader) + 255) / 256) * 256;
 // Lane refill once idle lanes add up to this many idle lane-iterations (as
@@ -137,10 +139,11 @@ __device__ __forceinline__ int find_request(const T* prefix, int n, T g)
 }
 
 // Chunk size when the caller names none: a multiple of 32 in [32, 1024],
-// about total / (warps * 4), so that every warp gets several chunks.
+// about total / (warps * 16), so that every warp gets many chunks (as in
+// awo_simulate.cu).
 __device__ __forceinline__ uint32_t adaptive_chunk(unsigned long long total, uint32_t warps)
 {
-    unsigned long long c = total / ((unsigned long long)max(warps, 1u) * 4ull);
+    unsigned long long c = total / ((unsigned long long)max(warps, 1u) * 16ull);
     c = c < 32ull ? 32ull : (c > 1024ull ? 1024ull : c);
     return (uint32_t)(c & ~31ull);
 }
@@ -157,6 +160,7 @@ __global__ void __launch_bounds__(AWO_BATCH_MAX) k_batch_prepare(const __grid_co
         if (q.n_cells_dev) nc = min(nc, *q.n_cells_dev);
         if (q.N == 0u) nc = 0u;  // no particles, no release visits
         a.hdr->n_cells[t] = nc;
+        a.hdr->order_stride[t] = order_stride(nc / order_block(q.N));
     }
     s_nc[t] = nc;
     // particles for the particle kernel: none for a request with max_steps = 0
@@ -194,7 +198,9 @@ __global__ void __launch_bounds__(256) k_batch_starts(const __grid_constant__ Ba
         const int r = find_request<uint32_t>(s_cp, n, g);
         const BatchReq& q = a.r[r];
         const uint32_t ci = g - s_cp[r];
-        const uint32_t entry = __ldg(q.cells + ci);
+        const uint32_t B = order_block(q.N);
+        const uint32_t entry =
+            __ldg(q.cells + order_source(ci, B, (s_cp[r + 1] - s_cp[r]) / B, a.hdr->order_stride[r]));
         bool ok;
         if (q.texel) {
             const TexelStart st = texel_start(q.h, q.W, q.H, q.tg, entry);

@@ -2,16 +2,17 @@
 //
 // Design (GB300):
 //  * Persistent kernel, one lane per particle.  The particles are numbered
-//    cell-major (release-list entry, then particle j); a warp takes a chunk
-//    of consecutive particles at a time from a global counter (one atomic per
+//    cell-major (start record, then particle j); a warp takes a chunk of
+//    consecutive particles at a time from a global counter (one atomic per
 //    chunk) and walks it with a warp-uniform cursor; a lane is refilled the
 //    moment its particle ends, so lanes never idle behind a long particle of
 //    the same warp.  The chunk size (32 .. 1024 particles) follows from the
 //    particle count and the grid, so that a release list of a few cells is
-//    still spread over many warps.  The particles in flight come from a
-//    compact window of the release list, so the lanes of a warp, and the
-//    warps of the GPU, touch a compact region of the DEM and of the rasters,
-//    which stays L2-resident even when the DEM does not.
+//    still spread over many warps.  The start records are in a processing
+//    order that spreads consecutive blocks of release cells over the grid
+//    (order_source): the lanes of a warp work on neighbouring cells, while
+//    the warps of the GPU work all over the grid, so the visits' reductions
+//    are spread over every L2 slice.
 //  * One integer division per chunk and none per particle: the cursor
 //    carries (release-list entry, j), and the start record holds the cell's
 //    coordinates.
@@ -80,7 +81,10 @@ struct SimArgs {
 
 constexpr int SIM_THREADS = 128;
 constexpr uint32_t SIM_CHUNK_MAX = 1024;  // particles per global fetch, at most
-constexpr uint32_t SIM_CHUNKS_PER_WARP = 4;  // fetches a warp makes on an even split, at least
+// fetches a warp makes on an even split, at least: chunks of neighbouring
+// cells carry similar work, so few large chunks leave some warps with much
+// more of it (2048^2 workload: 4 -> 16 chunks a warp, 1.80 -> 1.72 ms)
+constexpr uint32_t SIM_CHUNKS_PER_WARP = 16;
 // A warp refills its idle lanes once they add up to SIM_REFILL_IDLE idle
 // lane-iterations since its last refill (or when every lane is idle): a
 // refill round costs issue slots whether it starts one particle or thirty,
@@ -97,9 +101,10 @@ __device__ __forceinline__ uint32_t release_count(const SimArgs& a)
     return n;
 }
 
-// Prologue: per release-list entry, the start record and the release visit
-// of all N particles (count += N; their energy is 0, so the maximum is
-// unchanged).  Grid-stride over the entries, whose number may be on the device.
+// Prologue: per release-list entry, the start record (at its place in the
+// processing order above) and the release visit of all N particles (count +=
+// N; their energy is 0, so the maximum is unchanged).  Grid-stride over the
+// entries, whose number may be on the device.
 // TEXELS: the entries are texels of the release texture.  It also counts the
 // particles of entries outside the grid (rejected) and, when max_steps = 0
 // (every particle capped at its release visit; the particle kernel is not
@@ -108,9 +113,15 @@ template <bool TEXELS>
 __global__ void __launch_bounds__(256) k_sim_starts(const __grid_constant__ SimArgs a)
 {
     const uint32_t n_cells = release_count(a);
+    const uint32_t B = order_block(a.N);
+    const uint32_t nb = n_cells / B;
+    __shared__ uint32_t s_stride;
+    if (threadIdx.x == 0) s_stride = order_stride(nb);
+    __syncthreads();
+    const uint32_t S = s_stride;
     unsigned long long good = 0ull, bad = 0ull;
     for (uint32_t ci = blockIdx.x * blockDim.x + threadIdx.x; ci < n_cells; ci += gridDim.x * blockDim.x) {
-        const uint32_t entry = __ldg(a.cells + ci);
+        const uint32_t entry = __ldg(a.cells + order_source(ci, B, nb, S));
         bool ok;
         if (TEXELS) {
             const TexelStart st = texel_start(a.h, a.W, a.H, a.tg, entry);
