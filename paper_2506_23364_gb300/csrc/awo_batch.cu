@@ -59,7 +59,7 @@ struct BatchHeader {
     uint32_t chunk;                                    // particles per chunk
     uint32_t pad;
     unsigned long long stats[AWO_BATCH_MAX][6];
-    uint32_t order_stride[AWO_BATCH_MAX];              // processing order of each request's entries
+    uint32_t order_sinv[AWO_BATCH_MAX];                // processing order of each request's entries
 };
 constexpr size_t BATCH_HEADER_BYTES = ((sizeof(BatchHeader) + 255) / 256) * 256;
 // Lane refill once idle lanes add up to this many idle lane-iterations (as
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(AWO_BATCH_MAX) k_batch_prepare(const __grid_co
         if (q.n_cells_dev) nc = min(nc, *q.n_cells_dev);
         if (q.N == 0u) nc = 0u;  // no particles, no release visits
         a.hdr->n_cells[t] = nc;
-        a.hdr->order_stride[t] = order_stride(nc / order_block(q.N));
+        a.hdr->order_sinv[t] = order_stride_inverse(nc / order_block(q.N));
     }
     s_nc[t] = nc;
     // particles for the particle kernel: none for a request with max_steps = 0
@@ -198,20 +198,20 @@ __global__ void __launch_bounds__(256) k_batch_starts(const __grid_constant__ Ba
         const int r = find_request<uint32_t>(s_cp, n, g);
         const BatchReq& q = a.r[r];
         const uint32_t ci = g - s_cp[r];
+        const uint32_t entry = __ldg(q.cells + ci);
         const uint32_t B = order_block(q.N);
-        const uint32_t entry =
-            __ldg(q.cells + order_source(ci, B, (s_cp[r + 1] - s_cp[r]) / B, a.hdr->order_stride[r]));
+        const uint32_t slot = order_slot(ci, B, (s_cp[r + 1] - s_cp[r]) / B, a.hdr->order_sinv[r]);
         bool ok;
         if (q.texel) {
             const TexelStart st = texel_start(q.h, q.W, q.H, q.tg, entry);
             ok = st.t != ~0u;
             if (ok) atomicAdd(q.count + st.vcell, q.N);
-            a.starts[q.starts_off + ci] = st;
+            a.starts[q.starts_off + slot] = st;
         } else {
             const CellStart st = cell_start(q.h, q.W, q.H, q.n_grid, entry);
             ok = st.xy != ~0u;
             if (ok) atomicAdd(q.count + entry, q.N);
-            *reinterpret_cast<CellStart*>(a.starts + q.starts_off + ci) = st;
+            *reinterpret_cast<CellStart*>(a.starts + q.starts_off + slot) = st;
         }
         // particles of entries outside the grid are rejected; with max_steps = 0
         // every particle is capped at its release visit (no particle kernel work)

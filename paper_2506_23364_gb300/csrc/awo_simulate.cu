@@ -10,9 +10,8 @@
 //    particle count and the grid, so that a release list of a few cells is
 //    still spread over many warps.  The start records are in a processing
 //    order that spreads consecutive blocks of release cells over the grid
-//    (order_source): the lanes of a warp work on neighbouring cells, while
-//    the warps of the GPU work all over the grid, so the visits' reductions
-//    are spread over every L2 slice.
+//    (order_slot): the lanes of a warp work on neighbouring cells, while the
+//    warps of the GPU work all over the grid and its memory partitions.
 //  * One integer division per chunk and none per particle: the cursor
 //    carries (release-list entry, j), and the start record holds the cell's
 //    coordinates.
@@ -101,8 +100,8 @@ __device__ __forceinline__ uint32_t release_count(const SimArgs& a)
     return n;
 }
 
-// Prologue: per release-list entry, the start record (at its place in the
-// processing order above) and the release visit of all N particles (count +=
+// Prologue: per release-list entry, the start record (at its slot in the
+// processing order of awo_particle.cuh) and the release visit of all N particles (count +=
 // N; their energy is 0, so the maximum is unchanged).  Grid-stride over the
 // entries, whose number may be on the device.
 // TEXELS: the entries are texels of the release texture.  It also counts the
@@ -115,24 +114,24 @@ __global__ void __launch_bounds__(256) k_sim_starts(const __grid_constant__ SimA
     const uint32_t n_cells = release_count(a);
     const uint32_t B = order_block(a.N);
     const uint32_t nb = n_cells / B;
-    __shared__ uint32_t s_stride;
-    if (threadIdx.x == 0) s_stride = order_stride(nb);
+    __shared__ uint32_t s_sinv;
+    if (threadIdx.x == 0) s_sinv = order_stride_inverse(nb);
     __syncthreads();
-    const uint32_t S = s_stride;
+    const uint32_t Sinv = s_sinv;
     unsigned long long good = 0ull, bad = 0ull;
     for (uint32_t ci = blockIdx.x * blockDim.x + threadIdx.x; ci < n_cells; ci += gridDim.x * blockDim.x) {
-        const uint32_t entry = __ldg(a.cells + order_source(ci, B, nb, S));
+        const uint32_t entry = __ldg(a.cells + ci), slot = order_slot(ci, B, nb, Sinv);
         bool ok;
         if (TEXELS) {
             const TexelStart st = texel_start(a.h, a.W, a.H, a.tg, entry);
             ok = st.t != ~0u;
             if (ok) atomicAdd(a.count + st.vcell, a.N);
-            static_cast<TexelStart*>(a.starts)[ci] = st;
+            static_cast<TexelStart*>(a.starts)[slot] = st;
         } else {
             const CellStart st = cell_start(a.h, a.W, a.H, a.n_grid, entry);
             ok = st.xy != ~0u;
             if (ok) atomicAdd(a.count + entry, a.N);
-            static_cast<CellStart*>(a.starts)[ci] = st;
+            static_cast<CellStart*>(a.starts)[slot] = st;
         }
         good += ok ? 1ull : 0ull;
         bad += ok ? 0ull : 1ull;
