@@ -546,10 +546,12 @@ __global__ void __launch_bounds__(RT_THREADS) k_release_texture_mask(const float
                                                                      uint32_t Wr, int64_t n, float scale,
                                                                      float t_lo, float t_hi,
                                                                      uint8_t* __restrict__ mask,
-                                                                     uint32_t* __restrict__ tile_count)
+                                                                     uint32_t* __restrict__ tile_count,
+                                                                     uint32_t tile0)
 {
     // the texture has fewer than 2^31 texels: 32-bit indices throughout
-    const uint32_t base = blockIdx.x * (uint32_t)RT_TILE + threadIdx.x * (uint32_t)RT_CELLS;
+    const uint32_t tile = tile0 + blockIdx.x;
+    const uint32_t base = tile * (uint32_t)RT_TILE + threadIdx.x * (uint32_t)RT_CELLS;
     const uint32_t n32 = (uint32_t)n;
     const float wm1 = __int2float_rn(W - 1), hm1 = __int2float_rn(H - 1);
     uint32_t b = 0u, a = 0u;
@@ -612,7 +614,104 @@ __global__ void __launch_bounds__(RT_THREADS) k_release_texture_mask(const float
     store_mask(mask, base, n, bits);
     int total;
     block_exclusive_scan(__popc(bits), &total);
-    if (threadIdx.x == 0) tile_count[blockIdx.x] = (uint32_t)total;
+    if (threadIdx.x == 0) tile_count[tile] = (uint32_t)total;
+}
+
+// Rows that share their tan^2 rows (R = 1, 2): texture rows b = 2^R j + 2^(R-1)
+// ... 2^R j + 2^(R-1) + 2^R - 1 all have their centres between DEM rows j and
+// j + 1, so their texels at one column interpolate the same two horizontal
+// interpolations, with their own vertical weights.  A block takes one tile
+// column (RT_TILE texels of a row; rows are whole tiles) of the 2^R rows of
+// group j = blockIdx.y, each thread a run of RT_CELLS texels in every row:
+// the tan^2 values and the horizontal interpolations are computed once for
+// the group, the vertical combination per row (the same operations, in the
+// same order, as k_release_texture_mask).  The 2^(R-1) rows above the first
+// group and below the last clamp their centres to the grid and take
+// k_release_texture_mask.
+template <int R, bool VEC>
+__global__ void __launch_bounds__(RT_THREADS) k_release_texture_rows(const float* __restrict__ tan2, int W, int H,
+                                                                     uint32_t Wr, int64_t n, float scale,
+                                                                     float t_lo, float t_hi,
+                                                                     uint8_t* __restrict__ mask,
+                                                                     uint32_t* __restrict__ tile_count)
+{
+    using T = TexRun<R>;
+    constexpr int ROWS = 1 << R;
+    const uint32_t tiles_per_row = Wr / (uint32_t)RT_TILE;
+    const int j = (int)blockIdx.y;
+    const uint32_t b0 = (uint32_t)j * ROWS + (ROWS >> 1);  // first texture row of the group
+    const uint32_t a = blockIdx.x * (uint32_t)RT_TILE + threadIdx.x * (uint32_t)RT_CELLS;
+    const float hm1 = __int2float_rn(H - 1), wm1 = __int2float_rn(W - 1);
+    float oy[ROWS], fy[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        const float v = texel_centre(b0 + r, scale, hm1);  // in [j, j + 1): floor j, no clamp
+        fy[r] = __fsub_rn(v, __int2float_rn(j));
+        oy[r] = __fsub_rn(1.0f, fy[r]);
+    }
+    const int row = j * W;  // dj = W: j + 1 <= H - 1
+    uint32_t bits[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) bits[r] = 0u;
+    const int A = (int)(a >> R);
+    if (A + T::DMIN >= 0 && A + T::DMAX + 1 <= W - 2) {
+        float top[T::NC], bot[T::NC];
+        const float* p = tan2 + row + A;
+#pragma unroll
+        for (int i = T::DMIN; i <= T::DMAX + 1; ++i) {
+            const int g = i & ~3;
+            const bool whole = VEC && g >= T::DMIN && g + 3 <= T::DMAX + 1;
+            if (whole && i == g) {
+                const float4 qt = __ldg(reinterpret_cast<const float4*>(p + i));
+                const float4 qb = __ldg(reinterpret_cast<const float4*>(p + W + i));
+                top[i - T::DMIN] = qt.x, top[i - T::DMIN + 1] = qt.y, top[i - T::DMIN + 2] = qt.z,
+                              top[i - T::DMIN + 3] = qt.w;
+                bot[i - T::DMIN] = qb.x, bot[i - T::DMIN + 1] = qb.y, bot[i - T::DMIN + 2] = qb.z,
+                              bot[i - T::DMIN + 3] = qb.w;
+            } else if (!whole) {
+                top[i - T::DMIN] = __ldg(p + i);
+                bot[i - T::DMIN] = __ldg(p + W + i);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RT_CELLS; ++k) {
+            const int c = T::delta(k) - T::DMIN;
+            const float fx = T::frac(k), ox = T::one_minus_frac(k);
+            const float tp = __fadd_rn(__fmul_rn(top[c], ox), __fmul_rn(top[c + 1], fx));
+            const float bt = __fadd_rn(__fmul_rn(bot[c], ox), __fmul_rn(bot[c + 1], fx));
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                const float Tk = __fadd_rn(__fmul_rn(tp, oy[r]), __fmul_rn(bt, fy[r]));
+                bits[r] |= ((t_lo <= Tk && Tk <= t_hi) ? 1u : 0u) << k;
+            }
+        }
+    } else {
+        // the run touches a row end: texel by texel, columns clamped as in the general path
+#pragma unroll 1
+        for (int k = 0; k < RT_CELLS; ++k) {
+            const float u = texel_centre(a + (uint32_t)k, scale, wm1);
+            const int i0 = __float2int_rd(u);
+            const float fx = __fsub_rn(u, __int2float_rn(i0));
+            const int o = row + i0, di = i0 + 1 < W ? 1 : 0;
+            const float t00 = __ldg(tan2 + o), t10 = __ldg(tan2 + o + di);
+            const float t01 = __ldg(tan2 + o + W), t11 = __ldg(tan2 + o + W + di);
+            const float ox = __fsub_rn(1.0f, fx);
+            const float tp = __fadd_rn(__fmul_rn(t00, ox), __fmul_rn(t10, fx));
+            const float bt = __fadd_rn(__fmul_rn(t01, ox), __fmul_rn(t11, fx));
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                const float Tk = __fadd_rn(__fmul_rn(tp, oy[r]), __fmul_rn(bt, fy[r]));
+                bits[r] |= ((t_lo <= Tk && Tk <= t_hi) ? 1u : 0u) << k;
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        store_mask(mask, (int64_t)(b0 + r) * Wr + a, n, bits[r]);
+        int total;
+        block_exclusive_scan(__popc(bits[r]), &total);
+        if (threadIdx.x == 0) tile_count[(b0 + r) * tiles_per_row + blockIdx.x] = (uint32_t)total;
+    }
 }
 
 static float tan2_of_degrees(double deg)
@@ -830,8 +929,35 @@ extern "C" awo_status awo_release_texture(const float* d_tan2, awo_grid g, int32
                 : release_log2 == 2 ? (vec ? k_release_texture_mask<2, true> : k_release_texture_mask<2, false>)
                 : release_log2 == 3 ? k_release_texture_mask<3, false>
                                     : k_release_texture_mask<-1, false>;
-    kern<<<tiles, RT_THREADS, 0, s>>>(d_tan2, g.width, g.height, (uint32_t)wr, n, scale, t_lo,
-                                                        t_hi, d_mask, tile_count);
+    if ((release_log2 == 1 || release_log2 == 2) && g.height >= 2 && wr % RT_TILE == 0) {
+        // rows are whole tiles: the row groups that share their tan^2 rows in
+        // one kernel, the 2^(r-1) clamped rows at each end in the other
+        const uint32_t tpr = (uint32_t)(wr / RT_TILE), edge = 1u << (release_log2 - 1);
+        const uint32_t last = edge + ((uint32_t)(g.height - 1) << release_log2);  // first bottom edge row
+        kern<<<edge * tpr, RT_THREADS, 0, s>>>(d_tan2, g.width, g.height, (uint32_t)wr, n, scale, t_lo, t_hi, d_mask,
+                                                tile_count, 0u);
+        kern<<<edge * tpr, RT_THREADS, 0, s>>>(d_tan2, g.width, g.height, (uint32_t)wr, n, scale, t_lo, t_hi, d_mask,
+                                                tile_count, last * tpr);
+        const dim3 grid(tpr, (unsigned)(g.height - 1));
+        if (release_log2 == 1) {
+            if (vec)
+                k_release_texture_rows<1, true><<<grid, RT_THREADS, 0, s>>>(d_tan2, g.width, g.height, (uint32_t)wr,
+                                                                           n, scale, t_lo, t_hi, d_mask, tile_count);
+            else
+                k_release_texture_rows<1, false><<<grid, RT_THREADS, 0, s>>>(d_tan2, g.width, g.height, (uint32_t)wr,
+                                                                            n, scale, t_lo, t_hi, d_mask, tile_count);
+        } else {
+            if (vec)
+                k_release_texture_rows<2, true><<<grid, RT_THREADS, 0, s>>>(d_tan2, g.width, g.height, (uint32_t)wr,
+                                                                           n, scale, t_lo, t_hi, d_mask, tile_count);
+            else
+                k_release_texture_rows<2, false><<<grid, RT_THREADS, 0, s>>>(d_tan2, g.width, g.height, (uint32_t)wr,
+                                                                            n, scale, t_lo, t_hi, d_mask, tile_count);
+        }
+    } else {
+        kern<<<tiles, RT_THREADS, 0, s>>>(d_tan2, g.width, g.height, (uint32_t)wr, n, scale, t_lo, t_hi, d_mask,
+                                          tile_count, 0u);
+    }
     k_release_scan<<<1, 1024, 0, s>>>(tile_count, tiles, tile_offset, d_n);
     launch_mask_scatter(d_mask, n, tiles, tile_offset, d_texels, s);
     return launch_status();

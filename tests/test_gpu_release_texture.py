@@ -74,6 +74,26 @@ def test_release_texture_load_paths(r, W, offset):
     assert np.array_equal(tex_got, tex_ref)
 
 
+@pytest.mark.parametrize("r,W,H,offset", [(1, 2048, 37, 0), (1, 2048, 2, 0), (2, 1024, 19, 0), (2, 1024, 2, 1),
+                                           (1, 4096, 5, 1), (2, 2048, 3, 0)])
+def test_release_texture_row_groups(r, W, H, offset):
+    """Textures whose rows are whole tiles (W 2^r a multiple of 4096, r = 1, 2)
+    take the row-group kernel: the 2^r texture rows between two tan^2 rows
+    share their horizontal interpolations, and the clamped rows at both ends
+    take the per-row kernel.  Aligned and unaligned tan^2, the smallest grids
+    (H = 2: one row group) and row ends included."""
+    h = inputs.fbm(W, 0.8, seed=W + H + r, relief=1800.0)[:H, :W].astype(np.float32)
+    g, t2 = _tan2(h, 10.0)
+    t2h = t2.cpu().numpy()
+    buf = torch.empty(H * W + offset, dtype=torch.float32, device="cuda")
+    buf[offset:] = t2.reshape(-1)
+    m_ref, tex_ref = oracle.release_texture(t2h, r, 29.0, 46.0)
+    m_got, tex_got = _gpu_release_texture(buf[offset:].view(H, W), g, r, 29.0, 46.0)
+    assert tex_ref.size > 100
+    assert np.array_equal(m_got, m_ref)
+    assert np.array_equal(tex_got, tex_ref)
+
+
 def test_release_texture_unaligned_mask_and_r0():
     h = inputs.fbm(200, 0.8, seed=3, relief=1500.0).astype(np.float32)
     g, t2 = _tan2(h, 10.0)
