@@ -600,6 +600,14 @@ def run_batched(args, R: Ranks, emit: bool = True) -> dict:
             "plain": {"value": steps_plain / (ms_plain / 1e3), "ms_per_pass": ms_plain,
                       "form": "each region alone, in sequence, same stream"},
             "speedup_vs_plain": ms_plain / ms_batch, "clocks": clk}
+    # the particle kernels' ALU/issue count over the whole pass (terrain,
+    # prologues and mipmaps of the 64 regions included, so a lower bound)
+    sms = torch.cuda.get_device_properties(R.device).multi_processor_count
+    mhz = clk.get("sm_max_mhz") or 2070.0
+    visits = steps_batch + sum(x["n_traj"] for x in st)
+    line["alu"] = {"frac_whole_pass": ALG_OPS_PER_VISIT * visits / (ms_batch / 1e3) / (sms * 128 * mhz * 1e6),
+                   "visits": visits, "alg_ops_per_unit": ALG_OPS_PER_VISIT,
+                   "peak_source": f"{sms} SMs x 128 lanes x {mhz:.0f} MHz"}
     if emit and R.rank == 0:
         print(json.dumps(line), flush=True)
     return line
