@@ -430,7 +430,7 @@ def _extensions(args, R: Ranks) -> dict:
     beside the headline so that they are measured in the same run."""
     import torch
 
-    keep = {"batched": ("value", "unit", "ms_per_step", "speedup_vs_plain", "rasters_equal_plain", "clocks"),
+    keep = {"batched": ("value", "unit", "ms_per_step", "speedup_vs_plain", "rasters_equal_plain", "alu", "clocks"),
             "served": ("value", "unit", "latency_ms", "ok", "mean_batch", "wall_s", "clocks"),
             "differentiable": ("forward_ms", "backward_ms", "particles", "moves", "fd_rel_err"),
             "parabola": ("value", "unit", "min_ms", "particles", "moves")}
