@@ -118,9 +118,19 @@ __global__ void __launch_bounds__(256) k_sim_starts(const __grid_constant__ SimA
     if (threadIdx.x == 0) s_sinv = order_stride_inverse(nb);
     __syncthreads();
     const uint32_t Sinv = s_sinv;
+    // the slot of the thread's entries, advanced per grid stride G (a
+    // multiple of B: B <= 32 divides the block size) instead of one 64-bit
+    // modulo per entry: entry ci + G is in block ci / B + G / B, same offset
+    const uint32_t G = gridDim.x * blockDim.x;
+    const uint32_t ci0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned long long step = nb ? ((unsigned long long)(G / B) * Sinv) % nb : 0ull;
+    unsigned long long sb = nb ? ((unsigned long long)(ci0 / B) * Sinv) % nb : 0ull;
     unsigned long long good = 0ull, bad = 0ull;
-    for (uint32_t ci = blockIdx.x * blockDim.x + threadIdx.x; ci < n_cells; ci += gridDim.x * blockDim.x) {
-        const uint32_t entry = __ldg(a.cells + ci), slot = order_slot(ci, B, nb, Sinv);
+    for (uint32_t ci = ci0; ci < n_cells; ci += G) {
+        const uint32_t slot = ci < nb * B ? (uint32_t)sb * B + (ci & (B - 1u)) : ci;  // = order_slot(ci)
+        sb += step;
+        if (sb >= nb) sb -= nb;
+        const uint32_t entry = __ldg(a.cells + ci);
         bool ok;
         if (TEXELS) {
             const TexelStart st = texel_start(a.h, a.W, a.H, a.tg, entry);
