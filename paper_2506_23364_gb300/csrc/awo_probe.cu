@@ -109,27 +109,26 @@ extern "C" awo_status awo_selftest_rcp_sqrt(uint32_t first, uint64_t count, uint
 
 // Every divisor b of the list (positive, finite) and every FP32 a with bits
 // in [bits(b) - span, bits(b)] (at least +0): div_rn_by_rcp of a (unsigned and
-// signed forms) and of -a (signed form) against the intrinsic.  Divisors in
-// turn, each spread over the whole grid.
+// signed forms) and of -a (signed form) against the intrinsic.  The
+// (divisor, offset) pairs are spread over the grid, so a long list of
+// divisors with short spans runs as fast as a short list with long ones.
 __global__ void __launch_bounds__(256) k_selftest_div(const float* __restrict__ divisors, uint32_t n_div,
                                                       uint32_t span, unsigned long long* mismatches)
 {
     unsigned long long bad = 0ull;
-    const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (uint32_t d = 0; d < n_div; ++d) {
+    const unsigned long long per = (unsigned long long)span + 1ull, total = per * n_div;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < total;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t d = (uint32_t)(i / per), off = (uint32_t)(i - (unsigned long long)d * per);
         const float b = __ldg(divisors + d);
         if (!(b > 0.0f && b <= 3.4028234663852886e38f)) continue;
         const uint32_t bb = __float_as_uint(b);
-        const uint32_t lo = span >= bb ? 0u : bb - span;
-        const float y = __frcp_rn(b);
-        for (unsigned long long i = tid; i <= (unsigned long long)(bb - lo); i += stride) {
-            const float a = __uint_as_float(lo + (uint32_t)i);
-            const uint32_t want = __float_as_uint(__fdiv_rn(a, b)), want_neg = __float_as_uint(__fdiv_rn(-a, b));
-            bad += __float_as_uint(div_rn_by_rcp<false>(a, b, y)) != want ? 1ull : 0ull;
-            bad += __float_as_uint(div_rn_by_rcp<true>(a, b, y)) != want ? 1ull : 0ull;
-            bad += __float_as_uint(div_rn_by_rcp<true>(-a, b, y)) != want_neg ? 1ull : 0ull;
-        }
+        if (off > bb) continue;
+        const float a = __uint_as_float(bb - off), y = __frcp_rn(b);
+        const uint32_t want = __float_as_uint(__fdiv_rn(a, b)), want_neg = __float_as_uint(__fdiv_rn(-a, b));
+        bad += __float_as_uint(div_rn_by_rcp<false>(a, b, y)) != want ? 1ull : 0ull;
+        bad += __float_as_uint(div_rn_by_rcp<true>(a, b, y)) != want ? 1ull : 0ull;
+        bad += __float_as_uint(div_rn_by_rcp<true>(-a, b, y)) != want_neg ? 1ull : 0ull;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);

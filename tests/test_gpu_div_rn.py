@@ -1,9 +1,10 @@
-"""The compose pass's division (segment width through its correctly rounded
-reciprocal and two quotient corrections, Markstein's method) against the
-IEEE division intrinsic: every dividend in [0, b] for the widths of the
+"""The compose and normals passes' division (divisor through its correctly
+rounded reciprocal and two quotient corrections, Markstein's method) against
+the IEEE division intrinsic: every dividend in [0, b] for the widths of the
 colour ramps the tests and the bench use, the binade below b for 1024 seeded
 random divisors over 2^-70 .. 2^70 (both sides of the fast path's range),
-and the range limits themselves."""
+every divisor significand in [1, 2) with the 256 dividends just below it,
+and the range limits themselves (dividends of both signs throughout)."""
 import numpy as np
 import pytest
 import torch
@@ -33,6 +34,15 @@ def test_random_divisors_binade_below():
     exp = rng.integers(-70, 71, 1024)
     d = (sig * np.exp2(exp.astype(np.float64))).astype(np.float32)
     assert _mismatches(d, 1 << 23) == 0
+
+
+def test_every_divisor_significand():
+    """All 2^23 divisors in [1, 2) (the result depends on the significands
+    only, within the fast path's range), each with the 256 dividends just
+    below it: quotients just under 1, where rounding to nearest is closest
+    to a tie."""
+    d = (np.arange(1 << 23, dtype=np.uint32) | np.uint32(0x3F800000)).view(np.float32)
+    assert _mismatches(d, 255) == 0
 
 
 @pytest.mark.parametrize("b", [2.0 ** -60, 2.0 ** 60, np.nextafter(np.float32(2.0 ** -60), np.float32(0)),
