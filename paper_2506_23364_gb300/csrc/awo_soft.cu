@@ -46,6 +46,7 @@ struct SoftArgs {
     double* grad_theta;    // 2 (backward)
     double* grad_w;        // per release entry, FP64 scratch (backward)
     unsigned long long* stats;  // 6
+    unsigned long long* next_item;  // work counter (zeroed with the stats)
     cudaTextureObject_t tex;    // texture view of h for the footprint gathers (k_soft<_, true>), or 0
 };
 
@@ -59,41 +60,102 @@ __device__ __forceinline__ uint32_t soft_count(const SoftArgs& a)
     return n;
 }
 
+// Start records, and the particles of entries outside the grid counted as
+// rejected (the particle kernel skips them).
 __global__ void __launch_bounds__(256) k_soft_starts(const __grid_constant__ SoftArgs a)
 {
     const uint32_t n_cells = soft_count(a);
-    for (uint32_t ci = blockIdx.x * blockDim.x + threadIdx.x; ci < n_cells; ci += gridDim.x * blockDim.x)
-        a.starts[ci] = cell_start(a.h, a.W, a.H, a.n_grid, __ldg(a.cells + ci));
+    unsigned long long bad = 0ull;
+    for (uint32_t ci = blockIdx.x * blockDim.x + threadIdx.x; ci < n_cells; ci += gridDim.x * blockDim.x) {
+        const CellStart st = cell_start(a.h, a.W, a.H, a.n_grid, __ldg(a.cells + ci));
+        a.starts[ci] = st;
+        bad += st.xy == ~0u ? 1ull : 0ull;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    if ((threadIdx.x & 31) == 0 && bad && a.stats) atomicAdd(a.stats + 5, bad * a.N);
 }
 
-// One soft particle.  GRAD = false: deposits; GRAD = true: gradient sums.
-// TEX: footprints by texture gather through a.tex (else by loads).
+constexpr int SOFT_THREADS = 128;
+constexpr uint32_t SOFT_CHUNK_MAX = 1024;
+constexpr uint32_t SOFT_CHUNKS_PER_WARP = 16;
+constexpr uint32_t SOFT_REFILL_IDLE = 4;
+
+// Soft particles, GRAD = false: deposits; GRAD = true: gradient sums.  TEX:
+// footprints by texture gather through a.tex (else by loads).  Persistent,
+// one lane per particle, with the lane refill of the particle kernels
+// (awo_simulate.cu): a warp takes chunks of consecutive particles (entry,
+// then particle j) and restarts a lane whose particle has ended, so a long
+// particle does not keep the other lanes of its warp idle.  Each loop
+// iteration is two moves from one Philox block (moves n and n + 1 take words
+// 0-1 and 2-3 of block n >> 1; lanes start at n = 0 and move in pairs).  Per
+// particle the arithmetic is that of the hard mode's moves plus the
+// survival, its tangents and the deposits, in a fixed order.
 template <bool GRAD, bool TEX>
-__device__ __forceinline__ void soft_particle(const SoftArgs& a, uint32_t ci, uint32_t j, double& sum_mu,
-                                              double& sum_k, unsigned long long& steps, bool& rejected)
+__global__ void __launch_bounds__(SOFT_THREADS) k_soft(const __grid_constant__ SoftArgs a)
 {
-    const uint4 st = __ldg(reinterpret_cast<const uint4*>(a.starts) + ci);
-    if (st.x == ~0u) {
-        rejected = true;
-        return;
-    }
-    const float w = __ldg(a.weight + ci);
-    const uint32_t sx = st.x & 0xffffu, sy = st.x >> 16;
-    const uint32_t cell = sy * (uint32_t)a.W + sx;
-    float u = __int2float_rn((int)sx), v = __int2float_rn((int)sy);
-    float z = __uint_as_float(st.y), dx = __uint_as_float(st.z), dy = __uint_as_float(st.w);
+    const int lane = threadIdx.x & 31;
+    const unsigned lane_lt = (1u << lane) - 1u;
+    const uint32_t n_cells = soft_count(a);
+    const unsigned long long total = (unsigned long long)n_cells * a.N;
+    const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    unsigned long long chunk = total / (warps * SOFT_CHUNKS_PER_WARP);
+    chunk = chunk < 32ull ? 32ull : (chunk > SOFT_CHUNK_MAX ? (unsigned long long)SOFT_CHUNK_MAX : chunk);
+    chunk &= ~31ull;
+    unsigned long long cur_t = 0ull, end_t = 0ull;
+    uint32_t cur_ci = 0u, cur_j = 0u, idle_acc = 0u;
+    bool exhausted = (total == 0ull);
+
+    // the lane's particle
+    bool live = false;
+    uint32_t ci = 0u, cell = 0u, j = 0u, n = 0u, last = 0u;
+    float u = 0.f, v = 0.f, z = 0.f, dx = 0.f, dy = 0.f, e = 0.f, S = 1.f, w = 0.f;
     float fx = 0.f, fy = 0.f, h00 = 0.f, h10 = 0.f, h01 = 0.f, h11 = 0.f;
-    float e = 0.f, S = 1.f;
-    uint32_t last = cell;
-    // forward: cumulative fixed-point deposit; backward: tangents and sums
-    long long Q = 0;
-    float tmu = 0.f, tk = 0.f, smu = 0.f, sk = 0.f, acc_mu = 0.f, acc_k = 0.f, acc_w = 0.f;
-    uint32_t n = 0;
-    // the Philox block of moves n and n + 1 (words 0-1, then 2-3): computed at
-    // even n only; the lanes of a warp start their particles together and
-    // step in lock-step, so the branch is uniform across active lanes
-    uint4 r = make_uint4(0u, 0u, 0u, 0u);
-    while (n < a.max_steps) {
+    long long Q = 0;  // forward: cumulative fixed-point deposit
+    float tmu = 0.f, tk = 0.f, smu = 0.f, sk = 0.f, acc_mu = 0.f, acc_k = 0.f, acc_w = 0.f;  // backward
+    // the lane's counters
+    double sum_mu = 0.0, sum_k = 0.0;
+    unsigned long long steps = 0ull, traj = 0ull;
+    bool pend = false;  // backward: an ended particle whose FP64 sums are still to be added
+
+    // End of the lane's particle: the remainder w S to its last cell
+    // (forward), or the last cell's term (backward; its FP64 sums are added
+    // by flush(), at the next refill round or at the end, where the warp's
+    // ended lanes take them together: FP64 issue slots are scarce on GB300,
+    // and issued here they would be taken once for every move at which some
+    // lane of the warp ends).
+    auto finish = [&]() {
+        steps += n;
+        if (GRAD) {
+            const float G = __ldg(a.grad + last);
+            acc_mu += G * smu;
+            acc_k += G * sk;
+            acc_w += G * S;
+            pend = true;
+        } else {
+            const long long Wq = __float2ll_rn(w * FIX_SCALE);
+            if (Wq != Q) atomicAdd(a.deposit + last, (unsigned long long)(Wq - Q));
+        }
+        live = false;
+    };
+    auto flush = [&]() {
+        if (GRAD && pend) {
+            sum_mu += (double)w * (double)acc_mu * (double)a.mu;  // d/dlog(mu) = mu d/dmu
+            sum_k += (double)w * (double)acc_k * (double)a.k;
+            atomicAdd(a.grad_w + ci, (double)acc_w);
+            pend = false;
+        }
+    };
+
+    // One move of a live lane's particle with random words WX, WY (the move
+    // loop of the hard mode: a particle ends at max_steps moves, with no
+    // direction, outside the grid, or when S < 1e-7 after a move).
+    auto move = [&](uint32_t WX, uint32_t WY) {
+        if (!live) return;
+        if (n >= a.max_steps) {
+            finish();
+            return;
+        }
         const float ox = __fsub_rn(1.0f, fx), oy = __fsub_rn(1.0f, fy);
         const float ga = __fadd_rn(__fmul_rn(__fsub_rn(h10, h00), oy), __fmul_rn(__fsub_rn(h11, h01), fy));
         const float gb = __fadd_rn(__fmul_rn(__fsub_rn(h01, h00), ox), __fmul_rn(__fsub_rn(h11, h10), fx));
@@ -104,20 +166,24 @@ __device__ __forceinline__ void soft_particle(const SoftArgs& a, uint32_t ci, ui
             gx = __fmul_rn(-ga, ginv);
             gy = __fmul_rn(-gb, ginv);
         }
-        const bool odd = (n & 1u) != 0u;
-        if (!odd) r = philox4x32_10(make_uint4(cell, j, n >> 1, 0u), a.keys);
-        const float xix = uniform_pm1(odd ? r.z : r.x);
-        const float xiy = uniform_pm1(odd ? r.w : r.y);
+        const float xix = uniform_pm1(WX);
+        const float xiy = uniform_pm1(WY);
         const float rx = __fadd_rn(__fadd_rn(__fmul_rn(a.P, dx), __fmul_rn(a.oneP, gx)), __fmul_rn(a.R, xix));
         const float ry = __fadd_rn(__fadd_rn(__fmul_rn(a.P, dy), __fmul_rn(a.oneP, gy)), __fmul_rn(a.R, xiy));
         const float r2 = __fadd_rn(__fmul_rn(rx, rx), __fmul_rn(ry, ry));
-        if (r2 == 0.0f) break;
+        if (r2 == 0.0f) {
+            finish();
+            return;
+        }
         const float rinv = rcp_sqrt_rn(r2);
         dx = __fmul_rn(rx, rinv);
         dy = __fmul_rn(ry, rinv);
         const float u1 = __fadd_rn(u, __fmul_rn(a.s, dx));
         const float v1 = __fadd_rn(v, __fmul_rn(a.s, dy));
-        if (!(u1 >= 0.0f && u1 <= a.Wm1 && v1 >= 0.0f && v1 <= a.Hm1)) break;
+        if (!(u1 >= 0.0f && u1 <= a.Wm1 && v1 >= 0.0f && v1 <= a.Hm1)) {
+            finish();
+            return;
+        }
         const Foot f = foot_at<TEX ? 1 : 0>(a, u1, v1);
         const float z1 = bilinear(f, __fsub_rn(1.0f, f.fx), __fsub_rn(1.0f, f.fy));
         const float e1 = __fsub_rn(__fadd_rn(__fsub_rn(e, __fmul_rn(a.kD, e)), __fsub_rn(z, z1)), a.muD);
@@ -157,37 +223,75 @@ __device__ __forceinline__ void soft_particle(const SoftArgs& a, uint32_t ci, ui
         h11 = f.h11;
         last = c1;
         ++n;
-        if (S1 < SOFT_S_MIN) break;
-    }
-    steps += n;
-    if (GRAD) {
-        const float G = __ldg(a.grad + last);
-        acc_mu += G * smu;
-        acc_k += G * sk;
-        acc_w += G * S;
-        sum_mu += (double)w * (double)acc_mu * (double)a.mu;  // d/dlog(mu) = mu d/dmu
-        sum_k += (double)w * (double)acc_k * (double)a.k;
-        atomicAdd(a.grad_w + ci, (double)acc_w);
-    } else {
-        const long long Wq = __float2ll_rn(w * FIX_SCALE);
-        if (Wq != Q) atomicAdd(a.deposit + last, (unsigned long long)(Wq - Q));
-    }
-}
+        if (S1 < SOFT_S_MIN) finish();
+    };
 
-template <bool GRAD, bool TEX>
-__global__ void __launch_bounds__(128) k_soft(const __grid_constant__ SoftArgs a)
-{
-    const uint64_t total = (uint64_t)soft_count(a) * a.N;
-    double sum_mu = 0.0, sum_k = 0.0;
-    unsigned long long steps = 0ull, traj = 0ull, bad = 0ull;
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t ci = (uint32_t)(t / a.N), j = (uint32_t)(t - (uint64_t)ci * a.N);
-        bool rejected = false;
-        soft_particle<GRAD, TEX>(a, ci, j, sum_mu, sum_k, steps, rejected);
-        bad += rejected ? 1ull : 0ull;
-        traj += rejected ? 0ull : 1ull;
+    while (true) {
+        // ---- refill idle lanes (as in k_simulate) ----
+        const unsigned idle = __ballot_sync(0xffffffffu, !live);
+        idle_acc += (uint32_t)__popc(idle);
+        if (idle != 0u && idle_acc >= SOFT_REFILL_IDLE && !exhausted) {
+            idle_acc = 0u;
+            flush();
+            if (cur_t >= end_t) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(a.next_item, chunk);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                exhausted = base >= total;
+                if (!exhausted) {
+                    cur_t = base;
+                    end_t = min(total, base + chunk);
+                    cur_ci = (uint32_t)(base / a.N);  // one division per chunk
+                    cur_j = (uint32_t)(base - (unsigned long long)cur_ci * a.N);
+                }
+            }
+            if (!exhausted) {
+                const unsigned long long left = end_t - cur_t;
+                const unsigned avail = left < 32ull ? (unsigned)left : 32u;
+                const unsigned want = (unsigned)__popc(idle);
+                const unsigned take = want < avail ? want : avail;
+                const unsigned rank = (unsigned)__popc(idle & lane_lt);
+                const bool mine = ((idle >> lane) & 1u) && rank < take;
+                uint32_t c = cur_ci, jj = cur_j;
+                advance(c, jj, rank < take ? rank : 0u, a.N);
+                uint4 st = make_uint4(~0u, 0u, 0u, 0u);
+                if (mine) st = __ldg(reinterpret_cast<const uint4*>(a.starts) + c);
+                // entries outside the grid are counted by k_soft_starts
+                if (mine && st.x != ~0u) {
+                    const uint32_t sx = st.x & 0xffffu, sy = st.x >> 16;
+                    live = true;
+                    ci = c;
+                    j = jj;
+                    cell = sy * (uint32_t)a.W + sx;
+                    last = cell;
+                    n = 0u;
+                    u = __int2float_rn((int)sx);
+                    v = __int2float_rn((int)sy);
+                    z = __uint_as_float(st.y);
+                    dx = __uint_as_float(st.z);
+                    dy = __uint_as_float(st.w);
+                    e = 0.f;
+                    S = 1.f;
+                    w = __ldg(a.weight + c);
+                    fx = fy = h00 = h10 = h01 = h11 = 0.f;
+                    Q = 0;
+                    tmu = tk = smu = sk = acc_mu = acc_k = acc_w = 0.f;
+                    ++traj;
+                }
+                advance(cur_ci, cur_j, take, a.N);
+                cur_t += take;
+            }
+        }
+        if (__ballot_sync(0xffffffffu, live) == 0u) {
+            if (exhausted) break;
+            continue;
+        }
+        // moves n and n + 1 from one Philox block: every live lane is at an even n
+        const uint4 r = philox4x32_10(make_uint4(cell, j, n >> 1, 0u), a.keys);
+        move(r.x, r.y);
+        move(r.z, r.w);
     }
+    flush();
     // FP64 reductions over the warp, then one atomic per warp
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -195,7 +299,6 @@ __global__ void __launch_bounds__(128) k_soft(const __grid_constant__ SoftArgs a
         sum_k += __shfl_xor_sync(0xffffffffu, sum_k, o);
         steps += __shfl_xor_sync(0xffffffffu, steps, o);
         traj += __shfl_xor_sync(0xffffffffu, traj, o);
-        bad += __shfl_xor_sync(0xffffffffu, bad, o);
     }
     if ((threadIdx.x & 31) == 0) {
         if (GRAD) {
@@ -205,7 +308,6 @@ __global__ void __launch_bounds__(128) k_soft(const __grid_constant__ SoftArgs a
         if (a.stats) {
             if (steps) atomicAdd(a.stats + 0, steps);
             if (traj) atomicAdd(a.stats + 1, traj);
-            if (bad) atomicAdd(a.stats + 5, bad);
         }
     }
 }
@@ -227,7 +329,8 @@ __global__ void k_fixed_to_real(const long long* __restrict__ q, int64_t n, doub
 
 struct SoftWs {
     unsigned long long stats[6];
-    unsigned long long pad[2];
+    unsigned long long next_item;  // work counter of k_soft, in particles
+    unsigned long long pad;
 };
 constexpr size_t SOFT_STARTS_OFF = 256;
 
@@ -278,6 +381,7 @@ static awo_status soft_setup(SoftArgs& a, const float* d_h, awo_grid g, const ui
     a.weight = d_weight;
     SoftWs* ws = static_cast<SoftWs*>(d_ws);
     a.stats = ws->stats;
+    a.next_item = &ws->next_item;
     a.starts = reinterpret_cast<CellStart*>(static_cast<char*>(d_ws) + SOFT_STARTS_OFF);
     a.grad_w = reinterpret_cast<double*>(static_cast<char*>(d_ws) + SOFT_STARTS_OFF +
                                          (size_t)n_cells_max * sizeof(CellStart));
@@ -285,10 +389,22 @@ static awo_status soft_setup(SoftArgs& a, const float* d_h, awo_grid g, const ui
     return AWO_OK;
 }
 
-static unsigned soft_blocks(const SoftArgs& a)
+// Persistent grid of k_soft: the SMs times the resident blocks of the instance.
+template <bool GRAD, bool TEX>
+static unsigned soft_blocks()
 {
-    const int64_t total = (int64_t)a.n_cells_max * a.N;
-    return stream_blocks(total, 128, 16);
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (cached[dev] == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_soft<GRAD, TEX>, SOFT_THREADS, 0) != cudaSuccess ||
+            b < 1)
+            b = 1;
+        cached[dev] = b;
+    }
+    return (unsigned)(sm_count() * cached[dev]);
 }
 
 }  // namespace awo
@@ -315,9 +431,9 @@ extern "C" awo_status awo_soft_forward(const float* d_h, awo_grid g, const uint3
     if (a.N > 0 && n_cells_max > 0) {
         k_soft_starts<<<stream_blocks((int64_t)n_cells_max, 256), 256, 0, s>>>(a);
         if (a.tex)
-            k_soft<false, true><<<soft_blocks(a), 128, 0, s>>>(a);
+            k_soft<false, true><<<soft_blocks<false, true>(), SOFT_THREADS, 0, s>>>(a);
         else
-            k_soft<false, false><<<soft_blocks(a), 128, 0, s>>>(a);
+            k_soft<false, false><<<soft_blocks<false, false>(), SOFT_THREADS, 0, s>>>(a);
         st = launch_status();
         if (st != AWO_OK) return st;
     }
@@ -348,9 +464,9 @@ extern "C" awo_status awo_soft_backward(const float* d_h, awo_grid g, const uint
     if (a.N > 0 && n_cells_max > 0) {
         k_soft_starts<<<stream_blocks((int64_t)n_cells_max, 256), 256, 0, s>>>(a);
         if (a.tex)
-            k_soft<true, true><<<soft_blocks(a), 128, 0, s>>>(a);
+            k_soft<true, true><<<soft_blocks<true, true>(), SOFT_THREADS, 0, s>>>(a);
         else
-            k_soft<true, false><<<soft_blocks(a), 128, 0, s>>>(a);
+            k_soft<true, false><<<soft_blocks<true, false>(), SOFT_THREADS, 0, s>>>(a);
     }
     if (n_cells_max > 0)
         k_to_float<<<stream_blocks((int64_t)n_cells_max, 256), 256, 0, s>>>(a.grad_w, n_cells_max, d_n_cells,
