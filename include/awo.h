@@ -280,6 +280,19 @@ awo_status awo_simulate(const float* d_h, awo_grid g, const uint32_t* d_cells,
 awo_status awo_dem_gather_path(const float* d_h, awo_grid g, void* stream, int32_t* texture);
 
 /*
+ * Kernel timing (a diagnostic of this library; the paper has no counterpart).
+ * Hands two CUDA events (cudaEvent_t, passed as void*, created by the
+ * caller) to the next awo_simulate call made from the calling host thread,
+ * which records them on its stream immediately before and after its particle
+ * kernel -- not around the output clear or the start-record prologue -- so
+ * that kernel can be timed alone (when the call launches no particle kernel,
+ * both are recorded after its work).  The events are consumed by that call
+ * (also when it returns an error before enqueueing, unrecorded then); NULL,
+ * NULL withdraws them.  AWO_EINVAL: exactly one of them NULL.
+ */
+awo_status awo_simulate_time_kernel(void* ev_start, void* ev_stop);
+
+/*
  * c (batched). Particle trajectories for many regions in one persistent
  * launch (the paper's workflow re-run for many regions and parameter sets;
  * Sec. 5.2 lets the user change the parameters interactively).  Every request

@@ -155,6 +155,7 @@ def lib() -> ctypes.CDLL:
         "awo_selftest_rcp_sqrt": (st, [u32, ctypes.c_uint64, vp, vp]),
         "awo_selftest_visit_cell": (st, [u32, ctypes.c_uint64, vp, vp]),
         "awo_selftest_div_rn": (st, [vp, u32, u32, vp, vp]),
+        "awo_simulate_time_kernel": (st, [vp, vp]),
     }
     for name, (res, args) in protos.items():
         fn = getattr(L, name)
@@ -535,6 +536,19 @@ def awo_selftest_div_rn(divisors: torch.Tensor, span: int, out: torch.Tensor, st
     _check(lib().awo_selftest_div_rn(_dev(divisors, torch.float32, None, "divisors"), int(divisors.numel()),
                                      int(span), _dev(out, torch.int64, 1, "out"), _stream(stream)),
            "awo_selftest_div_rn")
+
+
+def awo_simulate_time_kernel(start, stop):
+    """Hands two torch.cuda.Event objects (recorded once already, so that they
+    exist) to the next awo_simulate of this thread, which records them around
+    its particle kernel alone; None, None withdraws them."""
+    if (start is None) != (stop is None):
+        raise ValueError("give both events or neither")
+    a = ctypes.c_void_p(start.cuda_event) if start is not None else None
+    b = ctypes.c_void_p(stop.cuda_event) if stop is not None else None
+    if start is not None and (not a.value or not b.value):
+        raise ValueError("the events have not been created yet: record them once first")
+    _check(lib().awo_simulate_time_kernel(a, b), "awo_simulate_time_kernel")
 
 
 def stats_dict(stats: torch.Tensor) -> dict:

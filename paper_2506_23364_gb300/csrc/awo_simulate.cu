@@ -342,6 +342,17 @@ using namespace awo;
 
 static size_t starts_offset() { return 256; }
 
+// Events of awo_simulate_time_kernel for the next awo_simulate of this thread.
+static thread_local cudaEvent_t t_kernel_events[2] = {nullptr, nullptr};
+
+extern "C" awo_status awo_simulate_time_kernel(void* ev_start, void* ev_stop)
+{
+    if ((ev_start == nullptr) != (ev_stop == nullptr)) return AWO_EINVAL;
+    t_kernel_events[0] = static_cast<cudaEvent_t>(ev_start);
+    t_kernel_events[1] = static_cast<cudaEvent_t>(ev_stop);
+    return AWO_OK;
+}
+
 extern "C" awo_status awo_dem_gather_path(const float* d_h, awo_grid g, void* stream, int32_t* texture)
 {
     if (!d_h || !texture || !grid_ok(g)) return AWO_EINVAL;
@@ -358,6 +369,8 @@ extern "C" awo_status awo_simulate(const float* d_h, awo_grid g, const uint32_t*
                                    uint32_t n_cells_max, const awo_sim_params* p, uint32_t* d_count, float* d_maxe,
                                    awo_sim_stats* d_stats, void* d_ws, size_t ws_bytes, void* stream)
 {
+    const cudaEvent_t ev_start = t_kernel_events[0], ev_stop = t_kernel_events[1];  // consumed by this call
+    t_kernel_events[0] = t_kernel_events[1] = nullptr;
     if (!d_h || !d_count || !d_maxe || !d_ws || !grid_ok(g)) return AWO_EINVAL;
     if (n_cells_max > 0 && !d_cells) return AWO_EINVAL;
     if (!sim_params_ok(p, g)) return AWO_EINVAL;
@@ -424,21 +437,32 @@ extern "C" awo_status awo_simulate(const float* d_h, awo_grid g, const uint32_t*
     } else if (a.N > 0 && n_cells_max > 0) {
         const unsigned pro_blocks = stream_blocks((int64_t)n_cells_max, 256);
         const unsigned sms = (unsigned)sm_count();
-        if (texels) {
+        if (texels)
             k_sim_starts<true><<<pro_blocks, 256, 0, s>>>(a);
+        else
+            k_sim_starts<false><<<pro_blocks, 256, 0, s>>>(a);
+        if (ev_start && cudaEventRecord(ev_start, s) != cudaSuccess) return AWO_ECUDA;
+        if (texels) {
             if (a.tex)
                 k_simulate<true, true><<<sms * sim_blocks_per_sm<true, true>(), SIM_THREADS, 0, s>>>(a);
             else
                 k_simulate<true, false><<<sms * sim_blocks_per_sm<true, false>(), SIM_THREADS, 0, s>>>(a);
         } else {
-            k_sim_starts<false><<<pro_blocks, 256, 0, s>>>(a);
             if (a.tex)
                 k_simulate<false, true><<<sms * sim_blocks_per_sm<false, true>(), SIM_THREADS, 0, s>>>(a);
             else
                 k_simulate<false, false><<<sms * sim_blocks_per_sm<false, false>(), SIM_THREADS, 0, s>>>(a);
         }
+        if (ev_stop && cudaEventRecord(ev_stop, s) != cudaSuccess) return AWO_ECUDA;
         awo_status st = launch_status();
         if (st != AWO_OK) return st;
+    } else if (ev_start) {  // no particle kernel: an empty interval after the call's work
+        if (cudaEventRecord(ev_start, s) != cudaSuccess || cudaEventRecord(ev_stop, s) != cudaSuccess)
+            return AWO_ECUDA;
+    }
+    if (a.N > 0 && n_cells_max > 0 && a.max_steps == 0u && ev_start) {  // prologue only: an empty interval
+        if (cudaEventRecord(ev_start, s) != cudaSuccess || cudaEventRecord(ev_stop, s) != cudaSuccess)
+            return AWO_ECUDA;
     }
     if (d_stats) {
         if (cudaMemcpyAsync(d_stats, ws->stats, sizeof(awo_sim_stats), cudaMemcpyDeviceToDevice, s) !=
