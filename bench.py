@@ -66,9 +66,9 @@ ALG_OPS_PER_VISIT = 126
 #   atomic_busy: lts__d_atomic_input_cycles_active.avg.pct_of_peak_sustained_elapsed
 #     / 100, the share of cycles the L2's reduction units take input
 KERNEL_COUNTERS: dict[str, dict[str, float]] = {
-    "5a746eeea4569058": {"dram": (916.375808e6 + 188.956416e6) / 1754008332, "lts_frac": 0.76800450,
-                         "red_sectors": 2177672814 / 1754008332, "read_sectors": 32571801 / 1754008332,
-                         "atomic_busy": 0.52212105},
+    "21bee4ee6bfef80c": {"dram": (917.063680e6 + 189.185280e6) / 1754008332, "lts_frac": 0.77099731,
+                         "red_sectors": 2177706165 / 1754008332, "read_sectors": 32575163 / 1754008332,
+                         "atomic_busy": 0.52413501},
 }
 
 
