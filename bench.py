@@ -373,7 +373,8 @@ def run_awo(args, R: Ranks):
     value = total_steps_all / (ms_step_max / 1e3)
 
     # end to end through the API with host buffers: H2D of the DEM, D2H of the overlay (all levels)
-    e2e = _e2e(args, R, awo, w, ov, host_dem, lambda o: (o.terrain(lo, hi), o.simulate(params), o.overlay(w.gravity)),
+    e2e = _e2e(args, R, awo, w, ov, host_dem, lambda o: o.terrain(lo, hi),
+               lambda o: (o.simulate(params), o.overlay(w.gravity)),
                float(st["total_steps"]), total_steps_all)
 
     peaks = _peaks()
@@ -465,16 +466,22 @@ def _extensions(args, R: Ranks) -> dict:
     return out
 
 
-def _e2e(args, R, awo, w, ov, host_dem, run, steps_one, steps_all) -> dict:
+def _e2e(args, R, awo, w, ov, host_dem, terrain, particles, steps_one, steps_all) -> dict:
     """The same workload end to end through the public API: every step copies
-    its DEM from pinned host memory, runs the workflow and copies the whole
-    overlay (count and velocity, every mipmap level) back to pinned host
-    memory.  Pipelined form (the value): --e2e-instances workflow instances
-    (default 3) on as many CUDA streams take steps in turn, so the copies of
-    one step overlap the kernels of the next; 4 x --e2e-steps steps are timed
-    so that the unoverlapped first copy-in and last copy-out weigh little.
-    Serial form (reported beside it): one stream, each step synchronised
-    before the next."""
+    its DEM from pinned host memory, runs the workflow (terrain(o), then
+    particles(o): the particle run with its velocity and mipmap) and copies
+    the whole overlay (count and velocity, every mipmap level) back to pinned
+    host memory.  Pipelined form (the value): --e2e-instances workflow
+    instances (default 3) on as many CUDA streams take steps in turn, so the
+    copies of one step overlap the kernels of the next; 4 x --e2e-steps steps
+    are timed so that the unoverlapped first copy-in and last copy-out weigh
+    little.  The particle run of step k waits for the mipmap pass of step
+    k - 2: the particle kernel is persistent (it holds every SM until its
+    work runs out), so a mipmap pass that became ready behind two of them
+    would hold its step's copy-out, and with it a later step, for two whole
+    particle runs; neighbouring steps' particle kernels still share their
+    tails.  Serial form (reported beside it): one stream, each step
+    synchronised before the next."""
     import numpy as np
     import torch
 
@@ -492,13 +499,19 @@ def _e2e(args, R, awo, w, ov, host_dem, run, steps_one, steps_all) -> dict:
     bi = pin_dem.numel() * pin_dem.element_size()
     bo = sum(h.numel() * h.element_size() for _, h in insts[0][1])
 
-    def one(inst):
+    def one(inst, after=None):
         o, outs, s = inst
         with torch.cuda.stream(s):
             (o.q if w.quantised else o.h).copy_(pin_dem, non_blocking=True)
-            run(o)
+            terrain(o)
+            if after is not None:
+                s.wait_event(after)
+            particles(o)
+            done = torch.cuda.Event()
+            done.record(s)
             for d, h in outs:
                 h.copy_(d, non_blocking=True)
+        return done
 
     n = max(args.e2e_steps, 1)
     # serial: one instance, synchronised per step
@@ -524,8 +537,10 @@ def _e2e(args, R, awo, w, ov, host_dem, run, steps_one, steps_all) -> dict:
     for inst in insts[1:]:
         inst[2].wait_event(a)
     k_steps = 4 * n
+    lag = 2  # the particle run of step k waits for the mipmap pass of step k - lag
+    dones = []
     for k in range(k_steps):
-        one(insts[k % m])
+        dones.append(one(insts[k % m], dones[k - lag] if k >= lag else None))
     for inst in insts[1:]:
         s0.wait_stream(inst[2])
     b.record(s0)
@@ -534,7 +549,8 @@ def _e2e(args, R, awo, w, ov, host_dem, run, steps_one, steps_all) -> dict:
     del extra, insts
     return {"value": steps_all / (pipe_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": bi,
             "d2h_bytes_per_step": bo, "ms_per_step": pipe_ms, "steps": k_steps,
-            "form": f"{m} workflow instances on {m} CUDA streams, steps in turn (copies overlap the next step)",
+            "form": f"{m} workflow instances on {m} CUDA streams, steps in turn (copies overlap the next step; "
+                    f"step k's particle run after step k - {lag}'s mipmap pass)",
             "serial": {"value": steps_all / (serial_ms / 1e3), "ms_per_step": serial_ms, "steps": n,
                        "form": "1 stream, synchronised after every step"}}
 
