@@ -381,7 +381,10 @@ def run_awo(args, R: Ranks):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     sim_s = kern_ms / 1e3  # roofline denominators: the particle kernel's own launch
     sha = _kernel_sha()
-    kc = KERNEL_COUNTERS.get(sha, {})
+    # the counters are per visit of the 8192^2 workload's launch (its 6144^2 crop): other workloads (the
+    # long-trajectory ones, a release texture) visit differently, so they report none
+    same_launch = args.workload == "large" and not args.release_log2
+    kc = KERNEL_COUNTERS.get(sha, {}) if same_launch else {}
     traffic = kc.get("dram")
     # issue / ALU ceiling: 152 SMs x 128 lanes x SM clock (max clock of the run)
     sms = torch.cuda.get_device_properties(R.device).multi_processor_count
@@ -399,8 +402,10 @@ def run_awo(args, R: Ranks):
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
     # L2: the hardware's own utilisation of the L2 for this kernel (ncu), the
     # gather/reduction roofline fraction; sector rates beside it
-    l2 = {"frac": kc.get("lts_frac"), "source": "ncu lts__throughput.avg.pct_of_peak_sustained_elapsed, "
-                                                "6144^2 crop launch of the same kernel code",
+    l2 = {"frac": kc.get("lts_frac"), "source": ("ncu lts__throughput.avg.pct_of_peak_sustained_elapsed, "
+                                                 "6144^2 crop launch of the same kernel code") if same_launch else
+                                                ("none: the counters were taken on the 8192^2 workload "
+                                                 "(ncu figures for this workload are in the profiles)"),
           "reduction_units_busy": kc.get("atomic_busy"),
           "red_sector_ops_per_s": kc["red_sectors"] * visits / sim_s if kc else None,
           "read_sectors_per_s": kc["read_sectors"] * visits / sim_s if kc else None,
