@@ -88,6 +88,24 @@ awo_status awo_selftest_visit_cell(uint32_t first, uint64_t count, uint64_t* d_m
 awo_status awo_selftest_div_rn(const float* d_divisors, uint32_t n_divisors, uint32_t span, uint64_t* d_mismatches,
                                void* stream);
 
+/*
+ * Random words of the particle kernels (a check of this library's own
+ * generator; Philox4x32-10 is defined by Salmon, Moraes, Dror and Shaw,
+ * "Parallel Random Numbers: As Easy as 1, 2, 3", SC'11).  For i in [0, n):
+ *   d_out[4i .. 4i+3] = Philox4x32-10(counter d_counters[4i .. 4i+3],
+ *                                     key (seed low word, seed high word)),
+ * computed on the current device by the device function that the particle
+ * kernels draw their moves from (awo_simulate: counter (cell, j, n >> 1, 0)).
+ * Round keys: weyl_keys == 0 takes them from a table filled on the host (the
+ * single-request kernel's form), weyl_keys != 0 generates them in registers
+ * by the Weyl schedule (the batched kernel's form when its requests have
+ * different seeds).  d_counters and d_out: device uint32 [4n], 16-byte
+ * aligned, caller-owned; d_out is overwritten.  Asynchronous on `stream`.
+ * AWO_EINVAL: d_counters or d_out NULL or misaligned, or n < 0.
+ */
+awo_status awo_probe_philox(const uint32_t* d_counters, int64_t n, uint64_t seed, int32_t weyl_keys,
+                            uint32_t* d_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -156,6 +156,7 @@ def lib() -> ctypes.CDLL:
         "awo_selftest_visit_cell": (st, [u32, ctypes.c_uint64, vp, vp]),
         "awo_selftest_div_rn": (st, [vp, u32, u32, vp, vp]),
         "awo_simulate_time_kernel": (st, [vp, vp]),
+        "awo_probe_philox": (st, [vp, ctypes.c_int64, ctypes.c_uint64, i32, vp, vp]),
     }
     for name, (res, args) in protos.items():
         fn = getattr(L, name)
@@ -529,6 +530,18 @@ def awo_selftest_visit_cell(first: int, count: int, out: torch.Tensor, stream=No
     """Mismatches (into out, int64 [1] on the device) of the kernels' visited cell against nearest-centre."""
     _check(lib().awo_selftest_visit_cell(int(first), int(count), _dev(out, torch.int64, 1, "out"), _stream(stream)),
            "awo_selftest_visit_cell")
+
+
+def awo_probe_philox(counters: torch.Tensor, seed: int, weyl_keys: bool, out: torch.Tensor, stream=None):
+    """Philox4x32-10 words of the particle kernels for counters (int32 [n, 4]
+    on the device, the words' bits) into out (int32 [n, 4]); round keys from
+    the host table (weyl_keys False) or the Weyl schedule in registers."""
+    if counters.dim() != 2 or counters.shape[1] != 4:
+        raise ValueError("counters must be [n, 4]")
+    n = counters.shape[0]
+    _check(lib().awo_probe_philox(_dev(counters, torch.int32, None, "counters"), n, int(seed) & (2 ** 64 - 1),
+                                  1 if weyl_keys else 0, _dev(out, torch.int32, 4 * n, "out"), _stream(stream)),
+           "awo_probe_philox")
 
 
 def awo_selftest_div_rn(divisors: torch.Tensor, span: int, out: torch.Tensor, stream=None):

@@ -1,11 +1,14 @@
 // awo_probe.cu -- L2 scattered-load and scattered-reduction throughput probes,
-// and the self-test of the particle kernels' correctly rounded normalisation.
+// the self-tests of the particle kernels' correctly rounded normalisation,
+// visited cell and division, and their Philox words for given counters.
 //
 // A persistent grid (SMs x 8 blocks of 256 threads, enough warps to cover L2
 // latency) issues independent, hashed 4-byte accesses into a buffer sized by
 // the caller (an L2-resident size gives the L2 ceiling).  The hash is a
 // multiply-xorshift of (thread, round), so accesses spread over all L2
 // slices with no locality between lanes.
+#include <algorithm>
+
 #include "awo_internal.cuh"
 #include "awo_particle.cuh"
 #include "awo_probe.h"
@@ -91,9 +94,51 @@ __global__ void __launch_bounds__(256) k_selftest_visit(uint32_t first, unsigned
     if ((threadIdx.x & 31) == 0 && bad) atomicAdd(mismatches, bad);
 }
 
+// Philox4x32-10 words of the counters c[0 .. n), by the particle kernels'
+// device function with round keys K (a table from the host or the Weyl
+// schedule in registers, as the kernels take them).
+template <class K>
+__global__ void __launch_bounds__(256) k_probe_philox(const uint4* __restrict__ c, int64_t n, const K key,
+                                                      uint4* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = philox4x32_10(__ldg(c + i), key);
+}
+
 }  // namespace awo
 
 using namespace awo;
+
+extern "C" awo_status awo_probe_philox(const uint32_t* d_counters, int64_t n, uint64_t seed, int32_t weyl_keys,
+                                       uint32_t* d_out, void* stream)
+{
+    if (!d_counters || !d_out || n < 0) return AWO_EINVAL;
+    if ((((uintptr_t)d_counters) & 15u) != 0 || (((uintptr_t)d_out) & 15u) != 0) return AWO_EINVAL;
+    if (n == 0) return AWO_OK;
+    const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+    const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
+    const uint4* c = reinterpret_cast<const uint4*>(d_counters);
+    uint4* o = reinterpret_cast<uint4*>(d_out);
+    cudaStream_t s = as_stream(stream);
+    if (weyl_keys) {
+        KeysWeyl key;
+        key.k0 = k0;
+        key.k1 = k1;
+        k_probe_philox<KeysWeyl><<<blocks, 256, 0, s>>>(c, n, key, o);
+    } else {
+        // the round-key table as the single-request kernel's host code fills it
+        KeysTable key;
+        uint32_t a = k0, b = k1;
+        for (int r = 0; r < 10; ++r) {
+            key.k0[r] = a;
+            key.k1[r] = b;
+            a += 0x9E3779B9u;
+            b += 0xBB67AE85u;
+        }
+        k_probe_philox<KeysTable><<<blocks, 256, 0, s>>>(c, n, key, o);
+    }
+    return launch_status();
+}
 
 extern "C" awo_status awo_selftest_rcp_sqrt(uint32_t first, uint64_t count, uint64_t* d_mismatches, void* stream)
 {

@@ -170,6 +170,12 @@ def test_selftest_and_gather_path_host_validation(L):
     assert L.awo_simulate_time_kernel(fake, None) == awo.AWO_EINVAL  # one event only
     assert L.awo_simulate_time_kernel(None, fake) == awo.AWO_EINVAL
     assert L.awo_simulate_time_kernel(None, None) == awo.AWO_OK  # withdraws (nothing recorded)
+    assert L.awo_probe_philox(None, 4, 0, 0, fake, None) == awo.AWO_EINVAL
+    assert L.awo_probe_philox(fake, 4, 0, 0, None, None) == awo.AWO_EINVAL
+    assert L.awo_probe_philox(fake, -1, 0, 1, fake, None) == awo.AWO_EINVAL
+    assert L.awo_probe_philox(ctypes.c_void_p(264), 4, 0, 0, fake, None) == awo.AWO_EINVAL  # misaligned
+    assert L.awo_probe_philox(fake, 4, 0, 0, ctypes.c_void_p(264), None) == awo.AWO_EINVAL
+    assert L.awo_probe_philox(fake, 0, 0, 0, fake, None) == awo.AWO_OK  # nothing to draw
     t = ctypes.c_int32(7)
     assert L.awo_dem_gather_path(None, awo.grid(16, 16, 10.0), None, ctypes.byref(t)) == awo.AWO_EINVAL
     assert L.awo_dem_gather_path(fake, awo.grid(0, 16, 10.0), None, ctypes.byref(t)) == awo.AWO_EINVAL
